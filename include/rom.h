@@ -1,0 +1,212 @@
+/*
+ * rom.h -- C ABI of the GB300 (sm_103a) Random Ordinate Method library.
+ *
+ * The library solves the steady radiative transport equation
+ *     u . grad psi + sigma_T psi = sigma_S fint_S P(u', u) psi(u') du' + q,
+ *     psi = psi_Gamma on the inflow boundary (u . n < 0),
+ * (Li, Tang & Yang, arXiv 2407.12527, Sec. 1, eq. equ_1 / equ_1_bc) in X-Y
+ * geometry by the Random Ordinate Method (Sec. 3.1): for each of several
+ * ordinate sets ("samples") it solves the discrete ordinate system of
+ * eq. (equ_random) with inflow eq. (equ_random_bd), discretised in space by
+ * diamond difference on a uniform Cartesian grid with cell-centred unknowns
+ * (Sec. 2), by classical source iteration (Sec. 3.2, eq. psiexpansion), and
+ * averages the scalar fluxes over the samples (Sec. 4.1).  Every step runs in
+ * hand-written CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions shared by every call:
+ *   - A context is used by one host thread at a time.  All device work of a
+ *     context is issued on its stream (rom_set_stream), in order.
+ *   - Cell arrays are [J][I] (2D), x fastest, cell (i, j) centred at
+ *     (x_L + (i + 1/2) dx, y_B + (j + 1/2) dy), i = 0..I-1, j = 0..J-1.
+ *   - Input buffers are read during the call and never kept: the caller keeps
+ *     ownership and may reuse them as soon as the call returns (device inputs
+ *     of the *_device calls are copied on the context stream, and the call
+ *     waits for that copy).  Output buffers are caller-allocated.
+ *   - Every call returns ROM_OK (0) or a negative ROM_ERR_* code; the message
+ *     of the last error of a context is returned by rom_last_error.  A CUDA
+ *     error inside a call is reported as ROM_ERR_CUDA and leaves the context
+ *     in need of rom_destroy.
+ *   - Arithmetic: sweeps and source updates in FP32, the source-iteration
+ *     residual norms and the sample average in FP64.
+ */
+#ifndef ROM_GB300_H
+#define ROM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define ROM_OK 0
+#define ROM_ERR_INVALID_ARG (-1)   /* bad size, pointer, range, sigma_S >= sigma_T, q < 0 ... */
+#define ROM_ERR_CUDA (-2)          /* a CUDA runtime call or kernel failed                    */
+#define ROM_ERR_OOM (-3)           /* device or host allocation failed                         */
+#define ROM_ERR_NOT_CONVERGED (-4) /* some sample reached max_iter above tol                   */
+#define ROM_ERR_DIVERGED (-5)      /* a residual became NaN/Inf                                */
+#define ROM_ERR_STATE (-6)         /* call made before the data it needs was set               */
+#define ROM_ERR_UNSUPPORTED (-7)   /* option not built (e.g. dim = 3)                          */
+
+/* --------------------------------------------------------------- choices */
+#define ROM_SCHEME_DD 0   /* diamond difference (Sec. 2)                      */
+#define ROM_SCHEME_STEP 1 /* upwind step scheme (positive; not in the paper) */
+
+#define ROM_KERNEL_ISO 0    /* P = 1                                              */
+#define ROM_KERNEL_LINEAR 1 /* P = 1 + g cos(xi), eq. (anisotropic kernel)         */
+#define ROM_KERNEL_HG 2     /* Henyey-Greenstein (1-g^2)/(1+g^2-2g cos xi)^{3/2}   */
+
+#define ROM_KERNEL_FLAG_NORMALIZE 1 /* divide row l by sum_l' w_l' P(u_l', u_l)  (Remark, Sec. 3.1) */
+#define ROM_KERNEL_FLAG_RAW 2       /* use G(cc'+ss'+zz') instead of the mirror average in zeta    */
+
+#define ROM_FACE_XL 0 /* x = x_L */
+#define ROM_FACE_XR 1 /* x = x_R */
+#define ROM_FACE_YB 2 /* y = y_B */
+#define ROM_FACE_YT 3 /* y = y_T */
+
+#define ROM_QUAD_UNIFORM 0    /* 2D uniform set, Appendix A eq. (uniform2D): n1 = N, M = 4 N^2      */
+#define ROM_QUAD_GAUSS 1      /* 2D Gaussian set, Appendix A: n1 = N, M = 2 N (N + 1)               */
+#define ROM_QUAD_PRODUCT_GL 2 /* n1 positive Gauss-Legendre polar cosines x n2 azimuths, M = n1 n2 */
+
+typedef struct rom_ctx rom_ctx; /* opaque */
+
+/* Solver options (rom_default_options fills the defaults shown). */
+typedef struct rom_options {
+    int scheme;      /* ROM_SCHEME_DD                                                     */
+    int max_iter;    /* 10000: cap on source-iteration sweeps per sample                  */
+    double tol;      /* 1e-6: a sample stops when ||phi^k - phi^{k-1}||_2 < tol ||phi^k||_2 */
+    int fixed_iters; /* 0; > 0 runs exactly this many sweeps for every sample, tol unused  */
+    int check_every; /* 0 = device-side loop (one CUDA graph with a conditional node);     */
+                     /* > 0: the host reads the number of unconverged samples after every  */
+                     /* check_every sweeps                                                 */
+    int tile_g;      /* 0 = automatic; else ordinates per sweep work item (1, 2 or 4)      */
+} rom_options;
+
+/* Statistics of the last rom_solve. */
+typedef struct rom_stats {
+    int n_samples;
+    int iterations_max;      /* most sweeps any sample took                              */
+    int iterations_min;      /* fewest sweeps any sample took                            */
+    int n_not_converged;     /* samples that stopped at max_iter above tol               */
+    int64_t updates;         /* cell-ordinate updates: sum_s cells * M_s * sweeps_s      */
+    double residual_max;     /* largest final relative change of phi over the samples    */
+    double gpu_ms;           /* device time of the solve, CUDA events on the ctx stream  */
+    int64_t kernel_launches; /* kernels the solve launched (graph nodes counted per run) */
+} rom_stats;
+
+/* ------------------------------------------------------------- lifetime */
+
+/* Create a context on CUDA device `cuda_device` with its own non-blocking
+ * stream.  *out receives the handle (NULL on failure). */
+int rom_create(rom_ctx **out, int cuda_device);
+
+/* Free every device and host resource of the context (NULL is allowed). */
+void rom_destroy(rom_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none).  Owned by ctx. */
+const char *rom_last_error(const rom_ctx *ctx);
+
+/* Issue all later device work on `cuda_stream` (a cudaStream_t of the
+ * context's device; NULL restores the context's own stream).  The caller keeps
+ * the stream alive while the context uses it. */
+int rom_set_stream(rom_ctx *ctx, void *cuda_stream);
+
+void rom_default_options(rom_options *opt);
+int rom_set_options(rom_ctx *ctx, const rom_options *opt);
+
+/* ---------------------------------------------------------------- problem */
+
+/* Grid and coefficients (Sec. 1 eq. equ_1; Sec. 2 grid).  dim must be 2.
+ * n[0] = I, n[1] = J (>= 1 each); lo = (x_L, y_B), hi = (x_R, y_T) with hi > lo.
+ * sigma_t, sigma_s, q: host FP64 [J][I] with 0 <= sigma_S < sigma_T and q >= 0
+ * (the paper's hypotheses, Sec. 1).  Resets any inflow to vacuum. */
+int rom_set_grid(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3], const double hi[3],
+                 const double *sigma_t, const double *sigma_s, const double *q);
+
+/* As rom_set_grid with FP32 device arrays [J][I] on the context's device; they
+ * are copied on the context stream and may be reused once the call returns.
+ * The hypotheses on the coefficients are checked on the device. */
+int rom_set_grid_device(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3],
+                        const double hi[3], const float *sigma_t, const float *sigma_s,
+                        const float *q);
+
+/* Isotropic inflow psi_Gamma on one face (eq. equ_1_bc): host FP64 values per
+ * face cell (J for the x faces, I for the y faces), >= 0; NULL = vacuum. */
+int rom_set_inflow_isotropic(rom_ctx *ctx, int face, const double *psi_face);
+
+/* Inflow per ordinate on one face (eq. equ_random_bd): host FP64
+ * [M_total][face cells], the ordinate index running over all samples in the
+ * order of rom_set_ordinates / rom_set_ordinates_seed; only the values of
+ * ordinates entering through the face are used.  Requires the ordinates. */
+int rom_set_inflow_ordinates(rom_ctx *ctx, int face, const double *psi);
+
+/* Explicit ordinate sets (Sec. 3.1 step 2, or any DOM set): n_samples sets with
+ * m_per_sample[s] >= 1 ordinates each, concatenated.  dirs is host FP64
+ * [sum M][3] = (c, s, zeta) with c^2 + s^2 + zeta^2 = 1 (to 1e-6), weights
+ * [sum M] > 0.  Each ordinate sweeps from the x_L side if c >= 0 (else x_R) and
+ * from the y_B side if s >= 0 (else y_T). */
+int rom_set_ordinates(rom_ctx *ctx, int n_samples, const int32_t *m_per_sample,
+                      const double *dirs, const double *weights);
+
+/* Random ordinate sets generated on the device (Sec. 3.1, Sec. 4.2,
+ * eq. 2Dordinates_symmetry, eq. wl).  Sample s (0-based, global index
+ * first_sample + s) splits the first quadrant of (zeta, theta) into
+ * n_zeta[s] x n_theta[s] equal cells, draws one point uniformly in each and
+ * reflects it to the other quadrants; every weight is 1 / (4 n_zeta n_theta).
+ * The uniform numbers are the SplitMix64 sequence of `seed` at counters
+ * (global sample << 32) | (cell << 1) | {0: zeta, 1: theta}, top 53 bits.
+ * Ordinates are stored per sample in the order quadrant 1 (cell l = (i-1) n_theta + j),
+ * then the reflections l + m, l + 2m, l + 3m (m = n_zeta n_theta). */
+int rom_set_ordinates_seed(rom_ctx *ctx, uint64_t seed, int n_samples, const int32_t *n_zeta,
+                           const int32_t *n_theta);
+int rom_set_ordinates_seed_offset(rom_ctx *ctx, uint64_t seed, int first_sample, int n_samples,
+                                  const int32_t *n_zeta, const int32_t *n_theta);
+
+/* One deterministic DOM set as a single sample (Appendix A): see ROM_QUAD_*. */
+int rom_set_quadrature(rom_ctx *ctx, int kind, int n1, int n2);
+
+/* Fill a deterministic X-Y quadrature into host arrays (no context needed):
+ * dirs [M][3] = (c, s, zeta), weights [M]; *m_out receives M.  Pass dirs =
+ * weights = NULL to query M only.  Same sets as rom_set_quadrature. */
+int rom_quadrature_xy(int kind, int n1, int n2, double *dirs, double *weights, int32_t *m_out);
+
+/* Copy the context's ordinates (after the last set call) to host FP64
+ * arrays: dirs [M_total][3], weights [M_total]. */
+int rom_get_ordinates(rom_ctx *ctx, double *dirs, double *weights);
+
+/* Scattering kernel P (Sec. 1; eq. anisotropic kernel; eq. wl): kind
+ * ROM_KERNEL_*, asymmetry g in (-1, 1), flags ROM_KERNEL_FLAG_*.  Default ISO. */
+int rom_set_kernel(rom_ctx *ctx, int kind, double g, int flags);
+
+/* ------------------------------------------------------------------ solve */
+
+/* Source iteration (Sec. 3.2, eq. psiexpansion) from psi = 0 for every sample,
+ * then the FP64 sample average (Sec. 4.1).  Returns ROM_OK, or
+ * ROM_ERR_NOT_CONVERGED / ROM_ERR_DIVERGED with the results still readable.
+ * stats_out may be NULL.  The call returns when the device work is done. */
+int rom_solve(rom_ctx *ctx, rom_stats *stats_out);
+
+/* Scalar flux phi = sum_l w_l psi_l at the cell centres (Sec. 2) into host FP64
+ * [J][I]: sample >= 0 one sample, sample = -1 the average over samples. */
+int rom_get_scalar_flux(rom_ctx *ctx, int sample, double *out);
+
+/* As rom_get_scalar_flux into a device FP64 buffer [J][I] (written on the
+ * context stream; the call returns after enqueueing the copy). */
+int rom_get_scalar_flux_device(rom_ctx *ctx, int sample, double *out);
+
+/* Sweeps each sample took and its last relative change (host arrays [n_samples]). */
+int rom_get_iterations(rom_ctx *ctx, int32_t *iters, double *residuals);
+
+/* Sum over this context's samples of phi (FP64 [J][I]) and their count, for
+ * combining runs over disjoint sample ranges (rom_set_ordinates_seed_offset). */
+int rom_get_partial_sum(rom_ctx *ctx, double *sum_out, int64_t *count_out);
+
+/* Library version string. */
+const char *rom_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROM_GB300_H */
