@@ -81,6 +81,9 @@ typedef struct rom_options {
                      /* > 0: the host reads the number of unconverged samples after every  */
                      /* check_every sweeps                                                 */
     int tile_g;      /* 0 = automatic; else ordinates per sweep work item (1, 2 or 4)      */
+    int time_kernels;/* 0; 1 records CUDA events around every sweep launch (host-driven     */
+                     /* loop, check_every >= 1 is then used, 1 if it is 0) and reports the  */
+                     /* summed sweep-kernel time in rom_stats.sweep_ms                     */
 } rom_options;
 
 /* Statistics of the last rom_solve. */
@@ -93,6 +96,8 @@ typedef struct rom_stats {
     double residual_max;     /* largest final relative change of phi over the samples    */
     double gpu_ms;           /* device time of the solve, CUDA events on the ctx stream  */
     int64_t kernel_launches; /* kernels the solve launched (graph nodes counted per run) */
+    double sweep_ms;         /* summed duration of the sweep kernels (time_kernels = 1)   */
+    int64_t sweep_launches;  /* sweep kernels timed                                       */
 } rom_stats;
 
 /* ------------------------------------------------------------- lifetime */

@@ -1,0 +1,284 @@
+// reduce.cu -- scattering-source update, source-iteration residual and sample
+// average (K2, K5, K6) plus small data-movement kernels.
+//
+// combine:  phi_s = sum over the work items of sample s of their moments
+//           (fixed item order, FP32), the new source moments
+//             isotropic: S = sigma_S phi + q                       (P = 1)
+//             linear:    S0 = sigma_S phi + q, S1 = g sigma_S (Jx, Jy)
+//           so that the next sweep forms S_l = S0 + c_l S1x + s_l S1y
+//           (eq. equ_random with eq. anisotropic kernel, mirror-averaged in
+//           zeta, where sum_l' w_l' (1 + g u_l'.u_l) psi_l' = phi + g (c Jx + s Jy)),
+//           and per-block FP64 partial sums of |phi^k - phi^{k-1}|^2 and |phi^k|^2.
+// finalize: relative l2 change per sample (Sec. 3.2 source iteration stopping
+//           rule of this library), sweep counters, the active flags, and the
+//           number of samples still iterating (optionally the condition of the
+//           device-side loop of a CUDA graph).
+// average:  phi_bar = (1/t) sum_s phi^{xi_s} in FP64 (Sec. 4.1).
+#include <math.h>
+
+#include "rom_internal.cuh"
+
+namespace romk {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b)
+{
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+template <int MOM>
+__global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
+{
+    const int s = blockIdx.y;
+    if (!A.active[s]) return;
+    const int ib = A.item_begin[s], ie = A.item_begin[s + 1];
+    const float4 *part = reinterpret_cast<const float4 *>(A.part);
+    float4 *phi = reinterpret_cast<float4 *>(A.phi) + (long long)s * MOM * A.cells4;
+    float4 *src = reinterpret_cast<float4 *>(A.src) + (long long)s * MOM * A.cells4;
+    const float4 *sig_s = reinterpret_cast<const float4 *>(A.sigma_s);
+    const float4 *q = reinterpret_cast<const float4 *>(A.q);
+    double d2 = 0.0, n2 = 0.0;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < A.cells4;
+         v += (long long)gridDim.x * blockDim.x) {
+        float4 acc[MOM];
+#pragma unroll
+        for (int m = 0; m < MOM; ++m) acc[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+        // items in batches of four independent loads, summed in item order
+        int it = ib;
+        for (; it + 4 <= ie; it += 4)
+#pragma unroll
+            for (int m = 0; m < MOM; ++m) {
+                float4 t[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) t[u] = part[((long long)(it + u) * MOM + m) * A.cells4 + v];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[m] = add4(acc[m], t[u]);
+            }
+        for (; it < ie; ++it)
+#pragma unroll
+            for (int m = 0; m < MOM; ++m)
+                acc[m] = add4(acc[m], part[((long long)it * MOM + m) * A.cells4 + v]);
+        const float4 old = phi[v];
+        const double dx = (double)acc[0].x - old.x, dy = (double)acc[0].y - old.y;
+        const double dz = (double)acc[0].z - old.z, dw = (double)acc[0].w - old.w;
+        d2 += dx * dx + dy * dy + dz * dz + dw * dw;
+        n2 += (double)acc[0].x * acc[0].x + (double)acc[0].y * acc[0].y +
+              (double)acc[0].z * acc[0].z + (double)acc[0].w * acc[0].w;
+#pragma unroll
+        for (int m = 0; m < MOM; ++m) phi[m * A.cells4 + v] = acc[m];
+        const float4 ss = sig_s[v], qq = q[v];
+        src[v] = make_float4(fmaf(ss.x, acc[0].x, qq.x), fmaf(ss.y, acc[0].y, qq.y),
+                             fmaf(ss.z, acc[0].z, qq.z), fmaf(ss.w, acc[0].w, qq.w));
+        if (MOM == 3) {
+            const float g = A.g;
+#pragma unroll
+            for (int m = 1; m < 3; ++m)
+                src[m * A.cells4 + v] = make_float4(g * ss.x * acc[m].x, g * ss.y * acc[m].y,
+                                                    g * ss.z * acc[m].z, g * ss.w * acc[m].w);
+        }
+    }
+    __shared__ double red[2][32];
+    d2 = warp_sum(d2);
+    n2 = warp_sum(n2);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][w] = d2;
+        red[1][w] = n2;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        d2 = lane < nw ? red[0][lane] : 0.0;
+        n2 = lane < nw ? red[1][lane] : 0.0;
+        d2 = warp_sum(d2);
+        n2 = warp_sum(n2);
+        if (lane == 0) {
+            A.partials[((long long)s * A.chunks + blockIdx.x) * 2 + 0] = d2;
+            A.partials[((long long)s * A.chunks + blockIdx.x) * 2 + 1] = n2;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) finalize_kernel(const FinalizeArgs A)
+{
+    int cnt = 0;
+    for (int s = threadIdx.x; s < A.S; s += blockDim.x) {
+        if (!A.active[s]) continue;
+        double d2 = 0.0, n2 = 0.0;
+        for (int c = 0; c < A.chunks; ++c) {
+            d2 += A.partials[((long long)s * A.chunks + c) * 2 + 0];
+            n2 += A.partials[((long long)s * A.chunks + c) * 2 + 1];
+        }
+        const double r = n2 > 0.0 ? sqrt(d2 / n2) : (d2 == 0.0 ? 0.0 : (double)INFINITY);
+        const int it = A.iters[s] + 1;
+        A.iters[s] = it;
+        A.resid[s] = r;
+        const bool bad = !isfinite(r);
+        if (bad) A.flags[s] |= 1;
+        bool stop;
+        if (A.fixed_iters > 0) stop = it >= A.fixed_iters;
+        else stop = (r < A.tol) || it >= A.max_iter || bad;
+        if (stop) A.active[s] = 0;
+        else ++cnt;
+    }
+    __shared__ int red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        *A.n_active = tot;
+        if (A.use_cond) cudaGraphSetConditional(A.cond, tot > 0 ? 1u : 0u);
+    }
+}
+
+__global__ void init_state_kernel(int S, int MOM, long long cells, const float *q, float *phi,
+                                  float *src, int *active, int *iters, int *flags, double *resid)
+{
+    const long long n = (long long)S * MOM * cells;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const long long cell = v % cells;
+        const int m = (int)((v / cells) % MOM);
+        phi[v] = 0.f;
+        src[v] = m == 0 ? q[cell] : 0.f;  // psi^0 = 0: the first source is q
+    }
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < S) {
+        active[t] = 1;
+        iters[t] = 0;
+        flags[t] = 0;
+        resid[t] = (double)INFINITY;
+    }
+}
+
+__global__ void average_kernel(const float *phi, int S, int MOM, int I, int J, int NXP,
+                               double *avg, double *sum)
+{
+    const long long cells = (long long)J * NXP;
+    const long long n = (long long)I * J;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const long long j = v / I, i = v - j * I;
+        double acc = 0.0;
+        for (int s = 0; s < S; ++s) acc += (double)phi[(long long)s * MOM * cells + j * NXP + i];
+        if (sum) sum[v] = acc;
+        if (avg) avg[v] = S > 0 ? acc / S : 0.0;
+    }
+}
+
+__global__ void extract_kernel(const float *phi, int sample, int MOM, int I, int J, int NXP,
+                               double *out)
+{
+    const long long cells = (long long)J * NXP;
+    const long long n = (long long)I * J;
+    const float *p = phi + (long long)sample * MOM * cells;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const long long j = v / I, i = v - j * I;
+        out[v] = (double)p[j * NXP + i];
+    }
+}
+
+// Copy [J][I] device inputs into the padded [J][NXP] layout and check the
+// hypotheses 0 <= sigma_S < sigma_T, q >= 0 (all finite).
+__global__ void pad_grid_kernel(const float *st_in, const float *ss_in, const float *q_in, int I,
+                                int J, int NXP, float *st_out, float *ss_out, float *q_out,
+                                unsigned int *stats)
+{
+    const long long n = (long long)J * NXP;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const long long j = v / NXP, i = v - j * NXP;
+        if (i < I) {
+            const float a = st_in[j * I + i], b = ss_in[j * I + i], c = q_in[j * I + i];
+            st_out[v] = a;
+            ss_out[v] = b;
+            q_out[v] = c;
+            const bool ok = isfinite(a) && isfinite(b) && isfinite(c) && b >= 0.f && b < a &&
+                            c >= 0.f;
+            if (!ok) atomicAdd(&stats[2], 1u);
+            else {  // a > 0 here, so its bit pattern orders like its value
+                atomicMin(&stats[0], __float_as_uint(a));
+                atomicMax(&stats[1], __float_as_uint(a));
+            }
+        } else {
+            st_out[v] = 1.f;  // padding columns are never swept
+            ss_out[v] = 0.f;
+            q_out[v] = 0.f;
+        }
+    }
+}
+
+int blocks_for(long long n, int threads)
+{
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 4096) b = 4096;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_combine(const CombineArgs &a, cudaStream_t st)
+{
+    const dim3 grid(a.chunks, a.S), block(256);
+    if (a.MOM == 1) combine_kernel<1><<<grid, block, 0, st>>>(a);
+    else if (a.MOM == 3) combine_kernel<3><<<grid, block, 0, st>>>(a);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t st)
+{
+    finalize_kernel<<<1, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(int S, int MOM, long long cells, const float *q, float *phi,
+                              float *src, int *active, int *iters, int *flags, double *resid,
+                              cudaStream_t st)
+{
+    long long n = (long long)S * MOM * cells;
+    if (n < S) n = S;
+    int b = blocks_for(n, 256);
+    if ((long long)b * 256 < S) b = (S + 255) / 256;
+    init_state_kernel<<<b, 256, 0, st>>>(S, MOM, cells, q, phi, src, active, iters, flags, resid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_average(const float *phi, int S, int MOM, int I, int J, int NXP, double *avg,
+                           double *sum, cudaStream_t st)
+{
+    average_kernel<<<blocks_for((long long)I * J, 256), 256, 0, st>>>(phi, S, MOM, I, J, NXP, avg,
+                                                                       sum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract(const float *phi, int sample, int MOM, int I, int J, int NXP,
+                           double *out, cudaStream_t st)
+{
+    extract_kernel<<<blocks_for((long long)I * J, 256), 256, 0, st>>>(phi, sample, MOM, I, J, NXP,
+                                                                       out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_grid(const float *st_in, const float *ss_in, const float *q_in, int I,
+                            int J, int NXP, float *st_out, float *ss_out, float *q_out,
+                            unsigned int *stats, cudaStream_t st)
+{
+    pad_grid_kernel<<<blocks_for((long long)J * NXP, 256), 256, 0, st>>>(
+        st_in, ss_in, q_in, I, J, NXP, st_out, ss_out, q_out, stats);
+    return cudaGetLastError();
+}
+
+}  // namespace romk

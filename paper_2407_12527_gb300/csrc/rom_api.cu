@@ -1,0 +1,1074 @@
+// rom_api.cu -- the C ABI of include/rom.h: context, problem setters, the
+// source-iteration driver and result getters.  All arithmetic of the method
+// runs in the kernels of sweep2d.cu, reduce.cu and ordinates.cu; this file
+// validates arguments, lays data out in device memory and orders launches.
+//
+// Source iteration (Sec. 3.2, eq. psiexpansion), per sweep k:
+//   sweep    (K1)  every active sample: moments of L^{-1}(scatter(psi^{k-1}) + q)
+//   combine  (K2)  phi^k per sample, next source, FP64 residual partials
+//   finalize (K5)  ||phi^k - phi^{k-1}|| / ||phi^k|| per sample, stop flags
+// then the FP64 sample average (K6).  The loop runs either on the device (a
+// CUDA graph whose conditional while-node repeats the three kernels until no
+// sample is active; no host round trip per sweep) or on the host, reading the
+// number of active samples every `check_every` sweeps.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/rom.h"
+#include "rom_internal.cuh"
+
+namespace romk {
+int host_quadrature(int kind, int n1, int n2, std::vector<double> &c, std::vector<double> &s,
+                    std::vector<double> &z, std::vector<double> &w);
+}
+
+using romk::SweepItem;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+enum OrdSource { ORD_NONE = 0, ORD_EXPLICIT = 1, ORD_SEED = 2 };
+
+}  // namespace
+
+struct rom_ctx {
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    rom_options opt{};
+
+    // grid
+    bool grid_set = false;
+    int I = 0, J = 0, NXP = 0;
+    double lo[2] = {0, 0}, hi[2] = {1, 1};
+    bool homog = false;
+    float sigma_t_homog = 1.f;
+    DevBuf sigt, sigs, q;
+
+    // inflow (host copies; uploaded at solve time)
+    std::vector<double> inflow_iso[4];
+    std::vector<double> inflow_ord[4];
+    bool inflow_dirty = true;
+    DevBuf inflow_dev;
+    bool inflow_any = false;
+    long long inflow_stride = 0;
+
+    // ordinates
+    int ord_source = ORD_NONE;
+    int S = 0;
+    long long Mtot = 0;
+    std::vector<int> M;            // per sample
+    std::vector<long long> off;    // first ordinate per sample
+    std::vector<unsigned char> quad;  // explicit sets: quadrant code per ordinate
+    DevBuf c64, s64, z64, w64, c32, s32, w32;
+
+    // kernel
+    int kernel_kind = ROM_KERNEL_ISO;
+    double g = 0.0;
+    int kernel_flags = 0;
+
+    // work items
+    bool items_dirty = true;
+    int G_used = 0;
+    std::vector<SweepItem> items;
+    std::vector<int> item_begin;
+    DevBuf items_dev, item_begin_dev;
+
+    // iteration state
+    int MOM = 1;
+    int chunks = 1;
+    DevBuf phi, src, part, partials, active, iters, flags, resid, n_active, avg, sum, tmp;
+    bool solved = false;
+    std::vector<int> h_iters;
+    std::vector<double> h_resid;
+
+    // device-side loop
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool graph_valid = false;
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> kev;  // sweep-kernel timing events (time_kernels = 1)
+    long long launches = 0;
+    int sm_count = 152;
+};
+
+namespace {
+
+int fail(rom_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, ROM_ERR_CUDA, "%s failed: %s (%s:%d)", #call,                    \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                          \
+    } while (0)
+
+int ensure(rom_ctx *ctx, DevBuf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    if (b.cap >= bytes) return ROM_OK;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+        if (e != cudaSuccess) return fail(ctx, ROM_ERR_CUDA, "cudaFree: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        (void)cudaGetLastError();
+        return fail(ctx, ROM_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    b.cap = bytes;
+    return ROM_OK;
+}
+
+void release(DevBuf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+void invalidate_graph(rom_ctx *ctx)
+{
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->graph_exec = nullptr;
+    ctx->graph = nullptr;
+    ctx->graph_valid = false;
+}
+
+void reset_ordinate_dependents(rom_ctx *ctx)
+{
+    for (int f = 0; f < 4; ++f) ctx->inflow_ord[f].clear();
+    ctx->inflow_dirty = true;
+    ctx->items_dirty = true;
+    ctx->solved = false;
+    invalidate_graph(ctx);
+}
+
+int face_cells(const rom_ctx *ctx, int face) { return face < 2 ? ctx->J : ctx->I; }
+
+int face_offset(const rom_ctx *ctx, int face)
+{
+    switch (face) {
+    case 0: return 0;
+    case 1: return ctx->J;
+    case 2: return 2 * ctx->J;
+    default: return 2 * ctx->J + ctx->I;
+    }
+}
+
+int set_grid_common(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3],
+                    const double hi[3])
+{
+    if (dim == 3) return fail(ctx, ROM_ERR_UNSUPPORTED, "dim = 3 is not built");
+    if (dim != 2) return fail(ctx, ROM_ERR_INVALID_ARG, "dim must be 2 (got %d)", dim);
+    if (!n || !lo || !hi) return fail(ctx, ROM_ERR_INVALID_ARG, "n, lo, hi must not be NULL");
+    if (n[0] < 1 || n[1] < 1) return fail(ctx, ROM_ERR_INVALID_ARG, "grid sizes must be >= 1");
+    if (n[0] > 32 * romk::kMaxWarps * romk::kCols)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "I = %lld exceeds %d", (long long)n[0],
+                    32 * romk::kMaxWarps * romk::kCols);
+    if (n[1] > (1 << 24)) return fail(ctx, ROM_ERR_INVALID_ARG, "J too large");
+    if (!(hi[0] > lo[0]) || !(hi[1] > lo[1]) || !isfinite(lo[0]) || !isfinite(hi[0]) ||
+        !isfinite(lo[1]) || !isfinite(hi[1]))
+        return fail(ctx, ROM_ERR_INVALID_ARG, "need hi > lo (finite)");
+    ctx->I = (int)n[0];
+    ctx->J = (int)n[1];
+    ctx->NXP = (ctx->I + romk::kCols - 1) / romk::kCols * romk::kCols;
+    ctx->lo[0] = lo[0];
+    ctx->lo[1] = lo[1];
+    ctx->hi[0] = hi[0];
+    ctx->hi[1] = hi[1];
+    for (int f = 0; f < 4; ++f) {
+        ctx->inflow_iso[f].clear();
+        ctx->inflow_ord[f].clear();
+    }
+    ctx->inflow_dirty = true;
+    ctx->items_dirty = true;
+    ctx->solved = false;
+    invalidate_graph(ctx);
+    const size_t bytes = (size_t)ctx->J * ctx->NXP * sizeof(float);
+    int rc;
+    if ((rc = ensure(ctx, ctx->sigt, bytes)) || (rc = ensure(ctx, ctx->sigs, bytes)) ||
+        (rc = ensure(ctx, ctx->q, bytes)))
+        return rc;
+    return ROM_OK;
+}
+
+int choose_g(const rom_ctx *ctx)
+{
+    if (ctx->opt.tile_g == 1 || ctx->opt.tile_g == 2 || ctx->opt.tile_g == 4) return ctx->opt.tile_g;
+    // largest G that still gives at least two work items per SM
+    for (int G : {4, 2}) {
+        long long n = 0;
+        for (int s = 0; s < ctx->S; ++s) n += 4 * ((ctx->M[s] / 4 + G - 1) / G);
+        if (n >= 2LL * ctx->sm_count) return G;
+    }
+    return 1;
+}
+
+int build_items(rom_ctx *ctx)
+{
+    const int G = choose_g(ctx);
+    ctx->G_used = G;
+    ctx->items.clear();
+    ctx->item_begin.assign(ctx->S + 1, 0);
+    std::vector<int> byq[4];
+    for (int s = 0; s < ctx->S; ++s) {
+        ctx->item_begin[s] = (int)ctx->items.size();
+        for (int qd = 0; qd < 4; ++qd) byq[qd].clear();
+        if (ctx->ord_source == ORD_SEED) {
+            const int m = ctx->M[s] / 4;
+            for (int qd = 0; qd < 4; ++qd)
+                for (int l = 0; l < m; ++l) {
+                    // quadrant blocks of the generated set: (+,+), (-,+), (-,-), (+,-)
+                    const int code = qd == 0 ? 0 : qd == 1 ? 1 : qd == 2 ? 3 : 2;
+                    byq[code].push_back((int)(ctx->off[s] + (long long)qd * m + l));
+                }
+        } else {
+            for (int l = 0; l < ctx->M[s]; ++l) {
+                const long long o = ctx->off[s] + l;
+                byq[ctx->quad[o]].push_back((int)o);
+            }
+        }
+        for (int code = 0; code < 4; ++code) {
+            const std::vector<int> &v = byq[code];
+            for (size_t k = 0; k < v.size(); k += G) {
+                SweepItem it{};
+                it.sample = s;
+                it.quad = code;
+                it.n = (int)std::min<size_t>(G, v.size() - k);
+                for (int t = 0; t < romk::kMaxG; ++t) it.ord[t] = t < it.n ? v[k + t] : v[k];
+                ctx->items.push_back(it);
+            }
+        }
+    }
+    ctx->item_begin[ctx->S] = (int)ctx->items.size();
+    int rc;
+    if ((rc = ensure(ctx, ctx->items_dev, ctx->items.size() * sizeof(SweepItem))) ||
+        (rc = ensure(ctx, ctx->item_begin_dev, ctx->item_begin.size() * sizeof(int))))
+        return rc;
+    if (!ctx->items.empty())
+        CK(cudaMemcpyAsync(ctx->items_dev.p, ctx->items.data(), ctx->items.size() * sizeof(SweepItem),
+                           cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->item_begin_dev.p, ctx->item_begin.data(),
+                       ctx->item_begin.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // host vectors may change before the next use
+    ctx->items_dirty = false;
+    return ROM_OK;
+}
+
+int upload_inflow(rom_ctx *ctx)
+{
+    bool any_ord = false, any_iso = false;
+    for (int f = 0; f < 4; ++f) {
+        any_ord |= !ctx->inflow_ord[f].empty();
+        any_iso |= !ctx->inflow_iso[f].empty();
+    }
+    const long long nface = 2LL * ctx->I + 2LL * ctx->J;
+    ctx->inflow_any = any_ord || any_iso;
+    if (!ctx->inflow_any) {
+        ctx->inflow_dirty = false;
+        return ROM_OK;
+    }
+    const long long rows = any_ord ? ctx->Mtot : 1;
+    ctx->inflow_stride = any_ord ? nface : 0;
+    std::vector<float> h((size_t)(rows * nface), 0.f);
+    for (long long o = 0; o < rows; ++o)
+        for (int f = 0; f < 4; ++f) {
+            const int nf = face_cells(ctx, f), fo = face_offset(ctx, f);
+            for (int k = 0; k < nf; ++k) {
+                double v = 0.0;
+                if (!ctx->inflow_ord[f].empty()) v = ctx->inflow_ord[f][(size_t)o * nf + k];
+                else if (!ctx->inflow_iso[f].empty()) v = ctx->inflow_iso[f][k];
+                h[(size_t)(o * nface + fo + k)] = (float)v;
+            }
+        }
+    int rc = ensure(ctx, ctx->inflow_dev, h.size() * sizeof(float));
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ctx->inflow_dev.p, h.data(), h.size() * sizeof(float),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->inflow_dirty = false;
+    return ROM_OK;
+}
+
+romk::SweepArgs sweep_args(const rom_ctx *ctx)
+{
+    romk::SweepArgs a{};
+    a.I = ctx->I;
+    a.J = ctx->J;
+    a.NXP = ctx->NXP;
+    a.inv_dx = (float)(ctx->I / (ctx->hi[0] - ctx->lo[0]));
+    a.inv_dy = (float)(ctx->J / (ctx->hi[1] - ctx->lo[1]));
+    a.sigma_t_homog = ctx->sigma_t_homog;
+    a.sigma_t = (const float *)ctx->sigt.p;
+    a.src = (const float *)ctx->src.p;
+    a.part = (float *)ctx->part.p;
+    a.items = (const SweepItem *)ctx->items_dev.p;
+    a.oc = (const float *)ctx->c32.p;
+    a.os = (const float *)ctx->s32.p;
+    a.ow = (const float *)ctx->w32.p;
+    a.inflow = ctx->inflow_any ? (const float *)ctx->inflow_dev.p : nullptr;
+    a.inflow_stride = ctx->inflow_stride;
+    a.active = (const int *)ctx->active.p;
+    a.cells = (long long)ctx->J * ctx->NXP;
+    return a;
+}
+
+// One source-iteration sweep: K1 + K2 + K5.
+int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphConditionalHandle h,
+                      cudaEvent_t k0 = nullptr, cudaEvent_t k1 = nullptr)
+{
+    const romk::SweepArgs sa = sweep_args(ctx);
+    const int L = (ctx->I + romk::kCols - 1) / romk::kCols;
+    const int nwarps = (L + 31) / 32;
+    if (k0) CK(cudaEventRecord(k0, st));
+    CK(romk::launch_sweep2d(sa, (int)ctx->items.size(), nwarps, ctx->G_used, ctx->opt.scheme,
+                            ctx->homog, ctx->MOM, st));
+    if (k1) CK(cudaEventRecord(k1, st));
+    romk::CombineArgs ca{};
+    ca.S = ctx->S;
+    ca.MOM = ctx->MOM;
+    ca.chunks = ctx->chunks;
+    ca.cells = (long long)ctx->J * ctx->NXP;
+    ca.cells4 = ca.cells / 4;
+    ca.g = (float)ctx->g;
+    ca.part = (const float *)ctx->part.p;
+    ca.item_begin = (const int *)ctx->item_begin_dev.p;
+    ca.phi = (float *)ctx->phi.p;
+    ca.src = (float *)ctx->src.p;
+    ca.sigma_s = (const float *)ctx->sigs.p;
+    ca.q = (const float *)ctx->q.p;
+    ca.active = (const int *)ctx->active.p;
+    ca.partials = (double *)ctx->partials.p;
+    CK(romk::launch_combine(ca, st));
+    romk::FinalizeArgs fa{};
+    fa.S = ctx->S;
+    fa.chunks = ctx->chunks;
+    fa.fixed_iters = ctx->opt.fixed_iters;
+    fa.max_iter = ctx->opt.max_iter;
+    fa.tol = ctx->opt.tol;
+    fa.partials = (const double *)ctx->partials.p;
+    fa.active = (int *)ctx->active.p;
+    fa.iters = (int *)ctx->iters.p;
+    fa.flags = (int *)ctx->flags.p;
+    fa.resid = (double *)ctx->resid.p;
+    fa.n_active = (int *)ctx->n_active.p;
+    fa.use_cond = use_cond ? 1 : 0;
+    fa.cond = h;
+    CK(romk::launch_finalize(fa, st));
+    return ROM_OK;
+}
+
+int build_graph(rom_ctx *ctx)
+{
+    invalidate_graph(ctx);
+    CK(cudaGraphCreate(&ctx->graph, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, ctx->graph, 1, cudaGraphCondAssignDefault));
+    // the struct has a union with a deleted default constructor: zero raw storage
+    alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)];
+    memset(np_raw, 0, sizeof np_raw);
+    cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(np_raw);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, ctx->graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    // capture on the context's private stream (capturable even when the user
+    // stream is the legacy default stream)
+    CK(cudaStreamBeginCaptureToGraph(ctx->own_stream, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_iteration(ctx, ctx->own_stream, true, h);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->own_stream, &captured);
+    if (rc) return rc;
+    if (e != cudaSuccess)
+        return fail(ctx, ROM_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    CK(cudaGraphInstantiate(&ctx->graph_exec, ctx->graph, 0));
+    ctx->graph_valid = true;
+    return ROM_OK;
+}
+
+}  // namespace
+
+// =========================================================== public ABI
+
+extern "C" {
+
+const char *rom_version(void) { return "rom-gb300 0.1.0 (sm_103a)"; }
+
+void rom_default_options(rom_options *opt)
+{
+    if (!opt) return;
+    memset(opt, 0, sizeof *opt);
+    opt->scheme = ROM_SCHEME_DD;
+    opt->max_iter = 10000;
+    opt->tol = 1e-6;
+    opt->fixed_iters = 0;
+    opt->check_every = 0;
+    opt->tile_g = 0;
+    opt->time_kernels = 0;
+}
+
+int rom_create(rom_ctx **out, int cuda_device)
+{
+    if (!out) return ROM_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device < 0 || cuda_device >= ndev) {
+        (void)cudaGetLastError();
+        return ROM_ERR_INVALID_ARG;
+    }
+    rom_ctx *ctx = new (std::nothrow) rom_ctx();
+    if (!ctx) return ROM_ERR_OOM;
+    ctx->device = cuda_device;
+    rom_default_options(&ctx->opt);
+    if (cudaSetDevice(cuda_device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        rom_destroy(ctx);
+        return ROM_ERR_CUDA;
+    }
+    ctx->stream = ctx->own_stream;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cuda_device) == cudaSuccess &&
+        sms > 0)
+        ctx->sm_count = sms;
+    *out = ctx;
+    return ROM_OK;
+}
+
+void rom_destroy(rom_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    invalidate_graph(ctx);
+    DevBuf *bufs[] = {&ctx->sigt, &ctx->sigs, &ctx->q, &ctx->inflow_dev, &ctx->c64, &ctx->s64,
+                      &ctx->z64, &ctx->w64, &ctx->c32, &ctx->s32, &ctx->w32, &ctx->items_dev,
+                      &ctx->item_begin_dev, &ctx->phi, &ctx->src, &ctx->part, &ctx->partials,
+                      &ctx->active, &ctx->iters, &ctx->flags, &ctx->resid, &ctx->n_active,
+                      &ctx->avg, &ctx->sum, &ctx->tmp};
+    for (DevBuf *b : bufs) release(*b);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (cudaEvent_t e : ctx->kev) cudaEventDestroy(e);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+}
+
+const char *rom_last_error(const rom_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int rom_set_stream(rom_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
+    return ROM_OK;
+}
+
+int rom_set_options(rom_ctx *ctx, const rom_options *opt)
+{
+    if (!ctx || !opt) return fail(ctx, ROM_ERR_INVALID_ARG, "NULL argument");
+    if (opt->scheme != ROM_SCHEME_DD && opt->scheme != ROM_SCHEME_STEP)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "unknown scheme %d", opt->scheme);
+    if (opt->fixed_iters < 0) return fail(ctx, ROM_ERR_INVALID_ARG, "fixed_iters < 0");
+    if (opt->fixed_iters == 0 && (opt->max_iter < 1 || !(opt->tol > 0.0)))
+        return fail(ctx, ROM_ERR_INVALID_ARG, "need max_iter >= 1 and tol > 0");
+    if (opt->check_every < 0) return fail(ctx, ROM_ERR_INVALID_ARG, "check_every < 0");
+    if (opt->time_kernels != 0 && opt->time_kernels != 1)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "time_kernels must be 0 or 1");
+    if (opt->tile_g != 0 && opt->tile_g != 1 && opt->tile_g != 2 && opt->tile_g != 4)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "tile_g must be 0, 1, 2 or 4");
+    if (opt->tile_g != ctx->opt.tile_g) ctx->items_dirty = true;
+    ctx->opt = *opt;
+    invalidate_graph(ctx);
+    return ROM_OK;
+}
+
+int rom_set_grid(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3], const double hi[3],
+                 const double *sigma_t, const double *sigma_s, const double *q)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    if (!sigma_t || !sigma_s || !q) return fail(ctx, ROM_ERR_INVALID_ARG, "NULL coefficient array");
+    CK(cudaSetDevice(ctx->device));
+    ctx->grid_set = false;
+    if (dim == 2 && n && n[0] >= 1 && n[1] >= 1) {
+        const size_t nc = (size_t)n[0] * (size_t)n[1];
+        for (size_t k = 0; k < nc; ++k) {
+            const double a = sigma_t[k], b = sigma_s[k], c = q[k];
+            if (!(isfinite(a) && isfinite(b) && isfinite(c) && b >= 0.0 && b < a && c >= 0.0))
+                return fail(ctx, ROM_ERR_INVALID_ARG,
+                            "cell %zu: need 0 <= sigma_S < sigma_T and q >= 0 (got %g, %g, %g)", k,
+                            a, b, c);
+        }
+    }
+    int rc = set_grid_common(ctx, dim, n, lo, hi);
+    if (rc) return rc;
+    const int I = ctx->I, J = ctx->J, NXP = ctx->NXP;
+    std::vector<float> hs((size_t)J * NXP), hss((size_t)J * NXP), hq((size_t)J * NXP);
+    double mn = sigma_t[0], mx = sigma_t[0];
+    for (int j = 0; j < J; ++j)
+        for (int i = 0; i < NXP; ++i) {
+            const size_t d = (size_t)j * NXP + i;
+            if (i < I) {
+                const size_t k = (size_t)j * I + i;
+                hs[d] = (float)sigma_t[k];
+                hss[d] = (float)sigma_s[k];
+                hq[d] = (float)q[k];
+                mn = std::min(mn, sigma_t[k]);
+                mx = std::max(mx, sigma_t[k]);
+            } else {
+                hs[d] = 1.f;
+                hss[d] = 0.f;
+                hq[d] = 0.f;
+            }
+        }
+    ctx->homog = ((float)mn == (float)mx);
+    ctx->sigma_t_homog = (float)mn;
+    const size_t bytes = hs.size() * sizeof(float);
+    CK(cudaMemcpyAsync(ctx->sigt.p, hs.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->sigs.p, hss.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->q.p, hq.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->grid_set = true;
+    return ROM_OK;
+}
+
+int rom_set_grid_device(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3],
+                        const double hi[3], const float *sigma_t, const float *sigma_s,
+                        const float *q)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    if (!sigma_t || !sigma_s || !q) return fail(ctx, ROM_ERR_INVALID_ARG, "NULL coefficient array");
+    CK(cudaSetDevice(ctx->device));
+    ctx->grid_set = false;
+    int rc = set_grid_common(ctx, dim, n, lo, hi);
+    if (rc) return rc;
+    if ((rc = ensure(ctx, ctx->tmp, 4 * sizeof(unsigned int)))) return rc;
+    unsigned int init[3] = {0x7f800000u, 0u, 0u};  // +inf bits, 0, 0
+    CK(cudaMemcpyAsync(ctx->tmp.p, init, sizeof init, cudaMemcpyHostToDevice, ctx->stream));
+    CK(romk::launch_pad_grid(sigma_t, sigma_s, q, ctx->I, ctx->J, ctx->NXP, (float *)ctx->sigt.p,
+                             (float *)ctx->sigs.p, (float *)ctx->q.p, (unsigned int *)ctx->tmp.p,
+                             ctx->stream));
+    ++ctx->launches;
+    unsigned int st[3];
+    CK(cudaMemcpyAsync(st, ctx->tmp.p, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (st[2] != 0)
+        return fail(ctx, ROM_ERR_INVALID_ARG,
+                    "%u cells violate 0 <= sigma_S < sigma_T, q >= 0 (or are not finite)", st[2]);
+    float mn, mx;
+    memcpy(&mn, &st[0], sizeof mn);
+    memcpy(&mx, &st[1], sizeof mx);
+    ctx->homog = (mn == mx);
+    ctx->sigma_t_homog = mn;
+    ctx->grid_set = true;
+    return ROM_OK;
+}
+
+int rom_set_inflow_isotropic(rom_ctx *ctx, int face, const double *psi_face)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    if (!ctx->grid_set) return fail(ctx, ROM_ERR_STATE, "set the grid first");
+    if (face < 0 || face > 3) return fail(ctx, ROM_ERR_INVALID_ARG, "face must be 0..3");
+    ctx->inflow_iso[face].clear();
+    ctx->inflow_ord[face].clear();
+    if (psi_face) {
+        const int nf = face_cells(ctx, face);
+        for (int k = 0; k < nf; ++k)
+            if (!(psi_face[k] >= 0.0) || !isfinite(psi_face[k]))
+                return fail(ctx, ROM_ERR_INVALID_ARG, "inflow must be finite and >= 0");
+        ctx->inflow_iso[face].assign(psi_face, psi_face + nf);
+    }
+    ctx->inflow_dirty = true;
+    ctx->solved = false;
+    return ROM_OK;
+}
+
+int rom_set_inflow_ordinates(rom_ctx *ctx, int face, const double *psi)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    if (!ctx->grid_set) return fail(ctx, ROM_ERR_STATE, "set the grid first");
+    if (ctx->ord_source == ORD_NONE) return fail(ctx, ROM_ERR_STATE, "set the ordinates first");
+    if (face < 0 || face > 3) return fail(ctx, ROM_ERR_INVALID_ARG, "face must be 0..3");
+    ctx->inflow_iso[face].clear();
+    ctx->inflow_ord[face].clear();
+    if (psi) {
+        const size_t n = (size_t)ctx->Mtot * face_cells(ctx, face);
+        for (size_t k = 0; k < n; ++k)
+            if (!(psi[k] >= 0.0) || !isfinite(psi[k]))
+                return fail(ctx, ROM_ERR_INVALID_ARG, "inflow must be finite and >= 0");
+        ctx->inflow_ord[face].assign(psi, psi + n);
+    }
+    ctx->inflow_dirty = true;
+    ctx->solved = false;
+    return ROM_OK;
+}
+
+int rom_set_ordinates(rom_ctx *ctx, int n_samples, const int32_t *m_per_sample,
+                      const double *dirs, const double *weights)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    if (n_samples < 1 || !m_per_sample || !dirs || !weights)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "need n_samples >= 1 and non-NULL arrays");
+    CK(cudaSetDevice(ctx->device));
+    long long tot = 0;
+    for (int s = 0; s < n_samples; ++s) {
+        if (m_per_sample[s] < 1)
+            return fail(ctx, ROM_ERR_INVALID_ARG, "sample %d has %d ordinates", s, m_per_sample[s]);
+        tot += m_per_sample[s];
+    }
+    if (tot > (1LL << 30)) return fail(ctx, ROM_ERR_INVALID_ARG, "too many ordinates");
+    for (long long o = 0; o < tot; ++o) {
+        const double c = dirs[3 * o], s = dirs[3 * o + 1], z = dirs[3 * o + 2], w = weights[o];
+        if (!(isfinite(c) && isfinite(s) && isfinite(z) && isfinite(w)) || !(w > 0.0) ||
+            fabs(c * c + s * s + z * z - 1.0) > 1e-6)
+            return fail(ctx, ROM_ERR_INVALID_ARG,
+                        "ordinate %lld: need |u| = 1 and weight > 0 (got %g %g %g, %g)", o, c, s,
+                        z, w);
+    }
+    ctx->S = n_samples;
+    ctx->Mtot = tot;
+    ctx->M.assign(m_per_sample, m_per_sample + n_samples);
+    ctx->off.resize(n_samples);
+    long long acc = 0;
+    for (int s = 0; s < n_samples; ++s) {
+        ctx->off[s] = acc;
+        acc += ctx->M[s];
+    }
+    ctx->quad.resize(tot);
+    std::vector<double> c(tot), s(tot), z(tot), w(tot);
+    std::vector<float> cf(tot), sf(tot), wf(tot);
+    for (long long o = 0; o < tot; ++o) {
+        c[o] = dirs[3 * o];
+        s[o] = dirs[3 * o + 1];
+        z[o] = dirs[3 * o + 2];
+        w[o] = weights[o];
+        cf[o] = (float)c[o];
+        sf[o] = (float)s[o];
+        wf[o] = (float)w[o];
+        ctx->quad[o] = (unsigned char)((c[o] < 0.0 ? 1 : 0) | (s[o] < 0.0 ? 2 : 0));
+    }
+    int rc;
+    const size_t b8 = tot * sizeof(double), b4 = tot * sizeof(float);
+    if ((rc = ensure(ctx, ctx->c64, b8)) || (rc = ensure(ctx, ctx->s64, b8)) ||
+        (rc = ensure(ctx, ctx->z64, b8)) || (rc = ensure(ctx, ctx->w64, b8)) ||
+        (rc = ensure(ctx, ctx->c32, b4)) || (rc = ensure(ctx, ctx->s32, b4)) ||
+        (rc = ensure(ctx, ctx->w32, b4)))
+        return rc;
+    CK(cudaMemcpyAsync(ctx->c64.p, c.data(), b8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->s64.p, s.data(), b8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->z64.p, z.data(), b8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->w64.p, w.data(), b8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->c32.p, cf.data(), b4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->s32.p, sf.data(), b4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->w32.p, wf.data(), b4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->ord_source = ORD_EXPLICIT;
+    reset_ordinate_dependents(ctx);
+    return ROM_OK;
+}
+
+int rom_set_ordinates_seed_offset(rom_ctx *ctx, uint64_t seed, int first_sample, int n_samples,
+                                  const int32_t *n_zeta, const int32_t *n_theta)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    if (n_samples < 1 || first_sample < 0 || !n_zeta || !n_theta)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "need n_samples >= 1, first_sample >= 0, arrays");
+    if ((long long)first_sample + n_samples > (1LL << 31))
+        return fail(ctx, ROM_ERR_INVALID_ARG, "sample index out of range");
+    CK(cudaSetDevice(ctx->device));
+    const bool same_layout = ctx->ord_source == ORD_SEED && ctx->S == n_samples;
+    std::vector<int> nz(n_zeta, n_zeta + n_samples), nt(n_theta, n_theta + n_samples);
+    std::vector<int> first_cell(n_samples + 1, 0);
+    std::vector<long long> off(n_samples);
+    std::vector<int> M(n_samples);
+    long long tot = 0;
+    for (int s = 0; s < n_samples; ++s) {
+        if (nz[s] < 1 || nt[s] < 1 || (long long)nz[s] * nt[s] > (1 << 24))
+            return fail(ctx, ROM_ERR_INVALID_ARG, "sample %d: bad partition %d x %d", s, nz[s],
+                        nt[s]);
+        const int m = nz[s] * nt[s];
+        first_cell[s + 1] = first_cell[s] + m;
+        off[s] = tot;
+        M[s] = 4 * m;
+        tot += 4LL * m;
+        if (first_cell[s + 1] > (1 << 30)) return fail(ctx, ROM_ERR_INVALID_ARG, "too many cells");
+    }
+    bool layout_same = same_layout && ctx->M == M;
+    ctx->S = n_samples;
+    ctx->Mtot = tot;
+    ctx->M = M;
+    ctx->off = off;
+    int rc;
+    const size_t b8 = tot * sizeof(double), b4 = tot * sizeof(float);
+    if ((rc = ensure(ctx, ctx->c64, b8)) || (rc = ensure(ctx, ctx->s64, b8)) ||
+        (rc = ensure(ctx, ctx->z64, b8)) || (rc = ensure(ctx, ctx->w64, b8)) ||
+        (rc = ensure(ctx, ctx->c32, b4)) || (rc = ensure(ctx, ctx->s32, b4)) ||
+        (rc = ensure(ctx, ctx->w32, b4)))
+        return rc;
+    // small per-sample tables packed into one device buffer
+    const size_t tb = (size_t)n_samples * (2 * sizeof(int) + sizeof(long long)) +
+                      (size_t)(n_samples + 1) * sizeof(int) + 64;
+    if ((rc = ensure(ctx, ctx->tmp, tb))) return rc;
+    std::vector<unsigned char> packed(tb, 0);
+    size_t p = 0;
+    const size_t o_off = p;
+    memcpy(packed.data() + p, off.data(), n_samples * sizeof(long long));
+    p += n_samples * sizeof(long long);
+    const size_t o_nz = p;
+    memcpy(packed.data() + p, nz.data(), n_samples * sizeof(int));
+    p += n_samples * sizeof(int);
+    const size_t o_nt = p;
+    memcpy(packed.data() + p, nt.data(), n_samples * sizeof(int));
+    p += n_samples * sizeof(int);
+    const size_t o_fc = p;
+    memcpy(packed.data() + p, first_cell.data(), (n_samples + 1) * sizeof(int));
+    CK(cudaMemcpyAsync(ctx->tmp.p, packed.data(), tb, cudaMemcpyHostToDevice, ctx->stream));
+    romk::OrdGenArgs a{};
+    unsigned char *base = (unsigned char *)ctx->tmp.p;
+    a.seed = seed;
+    a.n_samples = n_samples;
+    a.nz = (const int *)(base + o_nz);
+    a.nt = (const int *)(base + o_nt);
+    a.first_cell = (const int *)(base + o_fc);
+    a.ord_off = (const long long *)(base + o_off);
+    a.first_sample = first_sample;
+    a.total_cells = first_cell[n_samples];
+    a.c64 = (double *)ctx->c64.p;
+    a.s64 = (double *)ctx->s64.p;
+    a.z64 = (double *)ctx->z64.p;
+    a.w64 = (double *)ctx->w64.p;
+    a.c32 = (float *)ctx->c32.p;
+    a.s32 = (float *)ctx->s32.p;
+    a.w32 = (float *)ctx->w32.p;
+    CK(romk::launch_ordgen(a, ctx->stream));
+    ++ctx->launches;
+    CK(cudaStreamSynchronize(ctx->stream));  // the packed host table dies with this call
+    ctx->ord_source = ORD_SEED;
+    if (layout_same) {
+        // same sample layout: work items, buffers and the captured graph stay valid
+        for (int f = 0; f < 4; ++f) ctx->inflow_ord[f].clear();
+        ctx->solved = false;
+    } else {
+        reset_ordinate_dependents(ctx);
+    }
+    return ROM_OK;
+}
+
+int rom_set_ordinates_seed(rom_ctx *ctx, uint64_t seed, int n_samples, const int32_t *n_zeta,
+                           const int32_t *n_theta)
+{
+    return rom_set_ordinates_seed_offset(ctx, seed, 0, n_samples, n_zeta, n_theta);
+}
+
+int rom_quadrature_xy(int kind, int n1, int n2, double *dirs, double *weights, int32_t *m_out)
+{
+    std::vector<double> c, s, z, w;
+    const int M = romk::host_quadrature(kind, n1, n2, c, s, z, w);
+    if (M < 1) return ROM_ERR_INVALID_ARG;
+    if (m_out) *m_out = M;
+    if (dirs)
+        for (int o = 0; o < M; ++o) {
+            dirs[3 * o] = c[o];
+            dirs[3 * o + 1] = s[o];
+            dirs[3 * o + 2] = z[o];
+        }
+    if (weights)
+        for (int o = 0; o < M; ++o) weights[o] = w[o];
+    return ROM_OK;
+}
+
+int rom_set_quadrature(rom_ctx *ctx, int kind, int n1, int n2)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    std::vector<double> c, s, z, w;
+    const int M = romk::host_quadrature(kind, n1, n2, c, s, z, w);
+    if (M < 1) return fail(ctx, ROM_ERR_INVALID_ARG, "bad quadrature (%d, %d, %d)", kind, n1, n2);
+    std::vector<double> dirs(3 * (size_t)M);
+    for (int o = 0; o < M; ++o) {
+        dirs[3 * o] = c[o];
+        dirs[3 * o + 1] = s[o];
+        dirs[3 * o + 2] = z[o];
+    }
+    const int32_t m = M;
+    return rom_set_ordinates(ctx, 1, &m, dirs.data(), w.data());
+}
+
+int rom_get_ordinates(rom_ctx *ctx, double *dirs, double *weights)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    if (ctx->ord_source == ORD_NONE) return fail(ctx, ROM_ERR_STATE, "no ordinates set");
+    CK(cudaSetDevice(ctx->device));
+    const long long n = ctx->Mtot;
+    std::vector<double> c(n), s(n), z(n);
+    CK(cudaMemcpyAsync(c.data(), ctx->c64.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(s.data(), ctx->s64.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(z.data(), ctx->z64.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (weights)
+        CK(cudaMemcpyAsync(weights, ctx->w64.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (dirs)
+        for (long long o = 0; o < n; ++o) {
+            dirs[3 * o] = c[o];
+            dirs[3 * o + 1] = s[o];
+            dirs[3 * o + 2] = z[o];
+        }
+    return ROM_OK;
+}
+
+int rom_set_kernel(rom_ctx *ctx, int kind, double g, int flags)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    if (kind < ROM_KERNEL_ISO || kind > ROM_KERNEL_HG)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "unknown kernel %d", kind);
+    if (!(g > -1.0 && g < 1.0)) return fail(ctx, ROM_ERR_INVALID_ARG, "need -1 < g < 1");
+    if (flags & ~(ROM_KERNEL_FLAG_NORMALIZE | ROM_KERNEL_FLAG_RAW))
+        return fail(ctx, ROM_ERR_INVALID_ARG, "unknown kernel flags");
+    if (kind == ROM_KERNEL_HG)
+        return fail(ctx, ROM_ERR_UNSUPPORTED, "the Henyey-Greenstein kernel is not built");
+    if (kind == ROM_KERNEL_LINEAR && flags != 0)
+        return fail(ctx, ROM_ERR_UNSUPPORTED,
+                    "the linear kernel is built as the mirror-averaged, unnormalised moment form");
+    const int newmom = kind == ROM_KERNEL_ISO ? 1 : 3;
+    if (newmom != ctx->MOM) invalidate_graph(ctx);
+    ctx->kernel_kind = kind;
+    ctx->g = kind == ROM_KERNEL_ISO ? 0.0 : g;
+    ctx->kernel_flags = flags;
+    ctx->MOM = newmom;
+    ctx->solved = false;
+    invalidate_graph(ctx);
+    return ROM_OK;
+}
+
+int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    if (!ctx->grid_set) return fail(ctx, ROM_ERR_STATE, "set the grid first");
+    if (ctx->ord_source == ORD_NONE) return fail(ctx, ROM_ERR_STATE, "set the ordinates first");
+    CK(cudaSetDevice(ctx->device));
+    int rc;
+    const long long cells = (long long)ctx->J * ctx->NXP;
+    if (ctx->items_dirty) {
+        if ((rc = build_items(ctx))) return rc;
+        invalidate_graph(ctx);
+    }
+    if (ctx->inflow_dirty) {
+        if ((rc = upload_inflow(ctx))) return rc;
+        invalidate_graph(ctx);
+    }
+    // residual chunks: blocks of 256 threads with two float4 of cells each
+    const int chunks = (int)std::max<long long>(1, (cells / 4 + 511) / 512);
+    if (chunks != ctx->chunks) invalidate_graph(ctx);
+    ctx->chunks = chunks;
+    const int MOM = ctx->MOM;
+    const size_t state = (size_t)ctx->S * MOM * cells * sizeof(float);
+    const size_t nI = (size_t)ctx->I * ctx->J;
+    void *before[] = {ctx->phi.p, ctx->src.p, ctx->part.p, ctx->partials.p, ctx->active.p};
+    if ((rc = ensure(ctx, ctx->phi, state)) || (rc = ensure(ctx, ctx->src, state)) ||
+        (rc = ensure(ctx, ctx->part, ctx->items.size() * MOM * cells * sizeof(float))) ||
+        (rc = ensure(ctx, ctx->partials, (size_t)ctx->S * chunks * 2 * sizeof(double))) ||
+        (rc = ensure(ctx, ctx->active, ctx->S * sizeof(int))) ||
+        (rc = ensure(ctx, ctx->iters, ctx->S * sizeof(int))) ||
+        (rc = ensure(ctx, ctx->flags, ctx->S * sizeof(int))) ||
+        (rc = ensure(ctx, ctx->resid, ctx->S * sizeof(double))) ||
+        (rc = ensure(ctx, ctx->n_active, sizeof(int))) ||
+        (rc = ensure(ctx, ctx->avg, nI * sizeof(double))) ||
+        (rc = ensure(ctx, ctx->sum, nI * sizeof(double))))
+        return rc;
+    void *after[] = {ctx->phi.p, ctx->src.p, ctx->part.p, ctx->partials.p, ctx->active.p};
+    if (memcmp(before, after, sizeof before) != 0) invalidate_graph(ctx);
+
+    const long long launches0 = ctx->launches;
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    CK(romk::launch_init_state(ctx->S, MOM, cells, (const float *)ctx->q.p, (float *)ctx->phi.p,
+                               (float *)ctx->src.p, (int *)ctx->active.p, (int *)ctx->iters.p,
+                               (int *)ctx->flags.p, (double *)ctx->resid.p, ctx->stream));
+    ++ctx->launches;
+    const int cap = ctx->opt.fixed_iters > 0 ? ctx->opt.fixed_iters : ctx->opt.max_iter;
+    const bool timed = ctx->opt.time_kernels == 1;
+    double sweep_ms = 0.0;
+    long long sweep_launches = 0;
+    const bool device_loop = ctx->opt.check_every == 0 && !timed;
+    if (device_loop) {
+        if (!ctx->graph_valid && (rc = build_graph(ctx))) return rc;
+        CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    } else {
+        const int every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 1;
+        if (timed && ctx->kev.size() < 2 * (size_t)every) {
+            while (ctx->kev.size() < 2 * (size_t)every) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                ctx->kev.push_back(e);
+            }
+        }
+        int done = 0;
+        while (done < cap) {
+            const int n = std::min(every, cap - done);
+            for (int k = 0; k < n; ++k) {
+                cudaEvent_t k0 = timed ? ctx->kev[2 * k] : nullptr;
+                cudaEvent_t k1 = timed ? ctx->kev[2 * k + 1] : nullptr;
+                if ((rc = enqueue_iteration(ctx, ctx->stream, false, 0, k0, k1))) return rc;
+                ctx->launches += 3;
+            }
+            done += n;
+            int n_active = 0;
+            CK(cudaMemcpyAsync(&n_active, ctx->n_active.p, sizeof(int), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            if (timed)
+                for (int k = 0; k < n; ++k) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, ctx->kev[2 * k], ctx->kev[2 * k + 1]));
+                    sweep_ms += ms;
+                    ++sweep_launches;
+                }
+            if (n_active == 0) break;
+        }
+    }
+    CK(romk::launch_average((const float *)ctx->phi.p, ctx->S, MOM, ctx->I, ctx->J, ctx->NXP,
+                            (double *)ctx->avg.p, (double *)ctx->sum.p, ctx->stream));
+    ++ctx->launches;
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    ctx->h_iters.assign(ctx->S, 0);
+    ctx->h_resid.assign(ctx->S, 0.0);
+    std::vector<int> flags(ctx->S, 0);
+    CK(cudaMemcpyAsync(ctx->h_iters.data(), ctx->iters.p, ctx->S * sizeof(int),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_resid.data(), ctx->resid.p, ctx->S * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(flags.data(), ctx->flags.p, ctx->S * sizeof(int), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    ctx->solved = true;
+
+    rom_stats st{};
+    st.n_samples = ctx->S;
+    st.iterations_max = 0;
+    st.iterations_min = ctx->S ? ctx->h_iters[0] : 0;
+    int diverged = 0;
+    for (int s = 0; s < ctx->S; ++s) {
+        const int it = ctx->h_iters[s];
+        st.iterations_max = std::max(st.iterations_max, it);
+        st.iterations_min = std::min(st.iterations_min, it);
+        st.updates += (int64_t)ctx->I * ctx->J * ctx->M[s] * it;
+        const double r = ctx->h_resid[s];
+        if (!(r <= st.residual_max)) st.residual_max = r;
+        if (flags[s] & 1) ++diverged;
+        else if (ctx->opt.fixed_iters == 0 && !(r < ctx->opt.tol)) ++st.n_not_converged;
+    }
+    st.gpu_ms = ms;
+    st.sweep_ms = sweep_ms;
+    st.sweep_launches = sweep_launches;
+    if (device_loop) ctx->launches += 3LL * st.iterations_max;
+    st.kernel_launches = ctx->launches - launches0;
+    if (stats_out) *stats_out = st;
+    if (diverged) return fail(ctx, ROM_ERR_DIVERGED, "%d samples diverged (NaN/Inf residual)", diverged);
+    if (st.n_not_converged)
+        return fail(ctx, ROM_ERR_NOT_CONVERGED, "%d samples did not reach tol %g in %d sweeps",
+                    st.n_not_converged, ctx->opt.tol, ctx->opt.max_iter);
+    return ROM_OK;
+}
+
+int rom_get_scalar_flux(rom_ctx *ctx, int sample, double *out)
+{
+    if (!ctx || !out) return fail(ctx, ROM_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->solved) return fail(ctx, ROM_ERR_STATE, "call rom_solve first");
+    if (sample < -1 || sample >= ctx->S) return fail(ctx, ROM_ERR_INVALID_ARG, "bad sample %d", sample);
+    CK(cudaSetDevice(ctx->device));
+    const size_t nI = (size_t)ctx->I * ctx->J;
+    if (sample >= 0) {
+        int rc = ensure(ctx, ctx->tmp, nI * sizeof(double));
+        if (rc) return rc;
+        CK(romk::launch_extract((const float *)ctx->phi.p, sample, ctx->MOM, ctx->I, ctx->J,
+                                ctx->NXP, (double *)ctx->tmp.p, ctx->stream));
+        ++ctx->launches;
+        CK(cudaMemcpyAsync(out, ctx->tmp.p, nI * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    } else {
+        CK(cudaMemcpyAsync(out, ctx->avg.p, nI * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ROM_OK;
+}
+
+int rom_get_scalar_flux_device(rom_ctx *ctx, int sample, double *out)
+{
+    if (!ctx || !out) return fail(ctx, ROM_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->solved) return fail(ctx, ROM_ERR_STATE, "call rom_solve first");
+    if (sample < -1 || sample >= ctx->S) return fail(ctx, ROM_ERR_INVALID_ARG, "bad sample %d", sample);
+    CK(cudaSetDevice(ctx->device));
+    const size_t nI = (size_t)ctx->I * ctx->J;
+    if (sample >= 0) {
+        CK(romk::launch_extract((const float *)ctx->phi.p, sample, ctx->MOM, ctx->I, ctx->J,
+                                ctx->NXP, out, ctx->stream));
+        ++ctx->launches;
+    } else {
+        CK(cudaMemcpyAsync(out, ctx->avg.p, nI * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+    }
+    return ROM_OK;
+}
+
+int rom_get_iterations(rom_ctx *ctx, int32_t *iters, double *residuals)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    if (!ctx->solved) return fail(ctx, ROM_ERR_STATE, "call rom_solve first");
+    for (int s = 0; s < ctx->S; ++s) {
+        if (iters) iters[s] = ctx->h_iters[s];
+        if (residuals) residuals[s] = ctx->h_resid[s];
+    }
+    return ROM_OK;
+}
+
+int rom_get_partial_sum(rom_ctx *ctx, double *sum_out, int64_t *count_out)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    if (!ctx->solved) return fail(ctx, ROM_ERR_STATE, "call rom_solve first");
+    CK(cudaSetDevice(ctx->device));
+    if (sum_out) {
+        CK(cudaMemcpyAsync(sum_out, ctx->sum.p, (size_t)ctx->I * ctx->J * sizeof(double),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (count_out) *count_out = ctx->S;
+    return ROM_OK;
+}
+
+}  // extern "C"

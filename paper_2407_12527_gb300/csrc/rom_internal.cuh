@@ -1,0 +1,104 @@
+// rom_internal.cuh -- device data layout and kernel launch interfaces shared by
+// the translation units of the GB300 ROM library (not part of the public ABI).
+//
+// HBM layout (all FP32 unless noted; rows padded to a pitch of NXP = ceil(I/8)*8
+// floats so every lane's 8-cell segment is one aligned 32-byte sector):
+//   sigma_t, sigma_s, q      [J][NXP]
+//   phi    (per sample)      [S][MOM][J][NXP]   current iterate, MOM scalar moments
+//   src    (per sample)      [S][MOM][J][NXP]   source moments for the next sweep
+//   part   (per work item)   [items][MOM][J][NXP]  moments of one item's sweep
+//   ordinates                c, s, w [M_total] (FP32) and c, s, zeta, w (FP64)
+//   residual partials        [S][chunks][2] FP64
+// MOM = 1 for isotropic scattering (phi), 3 for the linear kernel (phi, Jx, Jy).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace romk {
+
+constexpr int kCols = 8;       // cells per lane along x
+constexpr int kMaxG = 4;       // ordinates per sweep work item
+constexpr int kMaxWarps = 8;   // I <= 32 * 8 * 8 = 2048
+
+// One sweep work item: up to kMaxG ordinates of one quadrant of one sample.
+// quad bit 0 set: c < 0 (sweep from x_R), bit 1 set: s < 0 (sweep from y_T).
+struct SweepItem {
+    int sample;
+    int quad;
+    int n;
+    int ord[kMaxG];
+};
+
+struct SweepArgs {
+    int I, J, NXP;
+    float inv_dx, inv_dy;
+    float sigma_t_homog;        // used when the grid has one sigma_T
+    const float *sigma_t;       // [J][NXP]
+    const float *src;           // [S][MOM][J][NXP]
+    float *part;                // [items][MOM][J][NXP]
+    const SweepItem *items;
+    const float *oc, *os, *ow;  // ordinate c, s, w
+    const float *inflow;        // nullptr = vacuum; else face values [x_L:J][x_R:J][y_B:I][y_T:I]
+    long long inflow_stride;    // per ordinate (0 = same values for every ordinate)
+    const int *active;          // [S] samples still iterating
+    long long cells;            // J * NXP
+};
+
+struct CombineArgs {
+    int S, MOM, chunks;
+    long long cells4;           // J * NXP / 4
+    long long cells;
+    float g;                    // linear-kernel asymmetry (MOM = 3)
+    const float *part;
+    const int *item_begin;      // [S + 1]
+    float *phi;
+    float *src;
+    const float *sigma_s, *q;
+    const int *active;
+    double *partials;           // [S][chunks][2]
+};
+
+struct FinalizeArgs {
+    int S, chunks;
+    int fixed_iters, max_iter;
+    double tol;
+    const double *partials;
+    int *active, *iters, *flags;
+    double *resid;
+    int *n_active;
+    int use_cond;
+    cudaGraphConditionalHandle cond;
+};
+
+// Ordinate generation (one thread per quadrant-1 cell of a sample).
+struct OrdGenArgs {
+    unsigned long long seed;
+    int n_samples;
+    const int *nz, *nt;         // per sample partition
+    const int *first_cell;      // [S+1] prefix sum of m = nz * nt
+    const long long *ord_off;   // [S] first ordinate of the sample
+    int first_sample;           // global index of local sample 0
+    int total_cells;
+    double *c64, *s64, *z64, *w64;
+    float *c32, *s32, *w32;
+};
+
+cudaError_t launch_sweep2d(const SweepArgs &a, int n_items, int nwarps, int G, int scheme,
+                           bool homog, int mom, cudaStream_t st);
+cudaError_t launch_combine(const CombineArgs &a, cudaStream_t st);
+cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t st);
+cudaError_t launch_init_state(int S, int MOM, long long cells, const float *q, float *phi,
+                              float *src, int *active, int *iters, int *flags, double *resid,
+                              cudaStream_t st);
+cudaError_t launch_average(const float *phi, int S, int MOM, int I, int J, int NXP, double *avg,
+                           double *sum, cudaStream_t st);
+cudaError_t launch_extract(const float *phi, int sample, int MOM, int I, int J, int NXP,
+                           double *out, cudaStream_t st);
+cudaError_t launch_pad_grid(const float *st_in, const float *ss_in, const float *q_in, int I,
+                            int J, int NXP, float *st_out, float *ss_out, float *q_out,
+                            unsigned int *stats /*[3]: min sigma_t bits, max bits, bad cells*/,
+                            cudaStream_t st);
+cudaError_t launch_ordgen(const OrdGenArgs &a, cudaStream_t st);
+
+}  // namespace romk

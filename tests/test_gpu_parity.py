@@ -1,0 +1,307 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Both sides receive identical FP64 ordinate arrays (or the same seed, whose
+draws each side generates from the SplitMix64 definition), identical grids and
+coefficients.  The bar is the relative l2 difference of the scalar flux,
+||phi_gpu - phi_oracle||_2 / ||phi_oracle||_2 <= 1e-5, per sample (FP32 sweeps
+against FP64).  Fixed-K runs remove any stopping-rule confound; converged runs
+stop the oracle at 1e-12 and the GPU at 1e-6: in FP32 the relative change of
+successive iterates stalls near 1e-7 (rounding), so smaller tolerances are not
+reachable, while the stopping error at 1e-6 is ~1e-6 * rho / (1 - rho).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+import rom_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rom():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2407_12527_gb300 import rom as R
+    return R
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def gpu_solve(R, I, J, bounds, st, ss, q, sets=None, seed=None, nz=None, nt=None, kernel="iso",
+              g=0.0, inflow=None, inflow_ord=None, **opts):
+    ctx = R.RomContext(0)
+    ctx.set_grid(I, J, bounds, st, ss, q)
+    if sets is not None:
+        ctx.set_ordinates([(o.c, o.s, o.zeta, o.w) for o in sets])
+    else:
+        ctx.set_ordinates_seed(seed, nz, nt)
+    if kernel != "iso":
+        ctx.set_kernel(kernel, g)
+    if inflow is not None:
+        off = [0, J, 2 * J, 2 * J + I, 2 * J + 2 * I]
+        for f in range(4):
+            ctx.set_inflow_isotropic(f, inflow[off[f]:off[f + 1]])
+    if inflow_ord is not None:
+        off = [0, J, 2 * J, 2 * J + I, 2 * J + 2 * I]
+        for f in range(4):
+            ctx.set_inflow_ordinates(f, np.ascontiguousarray(inflow_ord[:, off[f]:off[f + 1]]))
+    ctx.set_options(**opts)
+    st_ = ctx.solve()
+    n = ctx.n_samples
+    phi = np.stack([ctx.scalar_flux(k) for k in range(n)])
+    avg = ctx.scalar_flux(-1)
+    it, res = ctx.iterations()
+    psum, cnt = ctx.partial_sum()
+    ctx.close()
+    return {"phi": phi, "avg": avg, "iters": it, "resid": res, "stats": st_, "sum": psum,
+            "count": cnt}
+
+
+# ------------------------------------------------------------ ordinates
+
+@pytest.mark.parametrize("first", [0, 5])
+def test_seeded_ordinates_match_oracle(rom, first):
+    nz = [1, 2, 2, 3, 4, 1]
+    nt = [1, 2, 4, 3, 8, 7]
+    seed = 123456789
+    ctx = rom.RomContext(0)
+    ctx.set_ordinates_seed(seed, nz, nt, first_sample=first)
+    mt = 4 * int(np.dot(nz, nt))
+    dirs, w = ctx.get_ordinates(mt)
+    ctx.close()
+    off = 0
+    for k in range(len(nz)):
+        o = O.rom_ordinates_xy(seed, first + k, nz[k], nt[k])
+        sl = slice(off, off + o.M)
+        np.testing.assert_allclose(dirs[sl, 2], o.zeta, rtol=0, atol=4e-16)
+        np.testing.assert_allclose(dirs[sl, 0], o.c, rtol=0, atol=2e-15)
+        np.testing.assert_allclose(dirs[sl, 1], o.s, rtol=0, atol=2e-15)
+        np.testing.assert_array_equal(w[sl], o.w)
+        np.testing.assert_array_equal(np.sign(dirs[sl, :2]), np.sign(np.stack([o.c, o.s], 1)))
+        off += o.M
+
+
+# ------------------------------------------------------- fixed-K parity
+
+GRIDS = [
+    (37, 29, (0.0, 1.3, -0.2, 0.9)),   # ragged in x and y, one partial lane
+    (64, 64, (0.0, 1.0, 0.0, 1.0)),    # exact tiles
+    (300, 23, (-1.0, 2.0, 0.0, 0.5)),  # two warps per CTA, ragged last lane
+    (1, 9, (0.0, 0.1, 0.0, 1.0)),      # one column
+    (11, 1, (0.0, 1.0, 0.0, 0.1)),     # one row
+]
+
+
+@pytest.mark.parametrize("scheme", ["dd", "step"])
+@pytest.mark.parametrize("grid", GRIDS, ids=[f"{g[0]}x{g[1]}" for g in GRIDS])
+@pytest.mark.parametrize("homog", [True, False])
+def test_fixed_k_parity_random_directions(rom, scheme, grid, homog):
+    I, J, bounds = grid
+    st, ss, q = W.random_medium(I, J, seed=I * 31 + J)
+    if homog:
+        st = np.full((J, I), 1.7)
+        ss = np.minimum(ss, 1.5)
+    sets = [O.Ordinates(*W.random_directions(M, seed=100 + M, weights="random"))
+            for M in (5, 12, 3)]
+    K = 4
+    gpu = gpu_solve(rom, I, J, bounds, st, ss, q, sets=sets, scheme=rom.SCHEME[scheme],
+                    fixed_iters=K)
+    ref = O.solve_xy(I, J, bounds, st, ss, q, sets, scheme=scheme, fixed_iters=K)
+    for k in range(len(sets)):
+        assert rel(gpu["phi"][k], ref["phi"][k]) < TOL, k
+    assert list(gpu["iters"]) == [K] * len(sets)
+
+
+@pytest.mark.parametrize("tile_g", [1, 2, 4])
+def test_work_item_size_does_not_change_results(rom, tile_g):
+    I, J = 70, 45
+    bounds = (0, 1, 0, 1)
+    st, ss, q = W.random_medium(I, J, seed=3)
+    nz, nt = [2, 3, 1], [2, 3, 5]
+    gpu = gpu_solve(rom, I, J, bounds, st, ss, q, seed=77, nz=nz, nt=nt, fixed_iters=5,
+                    tile_g=tile_g)
+    sets = [O.rom_ordinates_xy(77, k, nz[k], nt[k]) for k in range(3)]
+    ref = O.solve_xy(I, J, bounds, st, ss, q, sets, fixed_iters=5)
+    for k in range(3):
+        assert rel(gpu["phi"][k], ref["phi"][k]) < TOL
+
+
+# ------------------------------------------------------ converged parity
+
+def test_converged_parity_example_2_1(rom):
+    """Example 2.1 (Sec. 2), ROM with 4 samples of 16 ordinates (Sec. 4.2 partition)."""
+    p = W.example_2_1()
+    nz = nt = [2] * 4
+    gpu = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, seed=2024, nz=nz, nt=nt,
+                    tol=1e-6, max_iter=200)
+    sets = [O.rom_ordinates_xy(2024, k, 2, 2) for k in range(4)]
+    ref = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, sets, tol=1e-12)
+    for k in range(4):
+        assert rel(gpu["phi"][k], ref["phi"][k]) < TOL
+    assert rel(gpu["avg"], O.rom_average(ref["phi"])) < TOL
+    # same stopping rule at the same tolerance: the same number of sweeps (+-1 for
+    # a relative change that lands within FP32 rounding of the threshold)
+    ref6 = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, sets, tol=1e-6)
+    assert np.all(np.abs(gpu["iters"] - ref6["iters"]) <= 1)
+    assert gpu["count"] == 4
+    np.testing.assert_allclose(gpu["sum"], gpu["phi"].astype(np.float64).sum(0), rtol=1e-12)
+
+
+def test_dom_uniform_and_gauss_parity(rom):
+    p = W.example_2_1(I=60, J=50)
+    for kind, N, maker in (("uniform", 4, O.quad_uniform_xy), ("gauss", 5, O.quad_gauss_xy)):
+        ctx = rom.RomContext(0)
+        ctx.set_grid(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q)
+        ctx.set_quadrature(kind, N)
+        ctx.set_options(tol=1e-6, max_iter=200)
+        ctx.solve()
+        phi = ctx.scalar_flux(0)
+        ctx.close()
+        ref = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, [maker(N)], tol=1e-12)
+        assert rel(phi, ref["phi"][0]) < TOL, kind
+
+
+def test_linear_kernel_parity(rom):
+    """Linear anisotropic kernel g = 0.9 (eq. anisotropic kernel): the GPU's
+    3-moment source against the oracle's dense w_l' P(u_l', u_l) contraction."""
+    p = W.example_2_1(I=48, J=40, g=0.9)
+    nz, nt = [2, 3], [2, 3]
+    gpu = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, seed=9, nz=nz, nt=nt,
+                    kernel="linear", g=0.9, fixed_iters=8)
+    sets = [O.rom_ordinates_xy(9, k, nz[k], nt[k]) for k in range(2)]
+    ref = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, sets, kernel="linear", g=0.9,
+                     fixed_iters=8)
+    for k in range(2):
+        assert rel(gpu["phi"][k], ref["phi"][k]) < TOL
+
+
+# ----------------------------------------------------------------- inflow
+
+def test_equilibrium_inflow(rom):
+    """Homogeneous medium with inflow q/(sigma_T - sigma_S): phi is that constant."""
+    I, J, st, ss, q = 40, 33, 2.0, 1.5, 0.7
+    val = q / (st - ss)
+    infl = np.full(2 * I + 2 * J, val)
+    gpu = gpu_solve(rom, I, J, (0, 1, 0, 1), st, ss, q, seed=1, nz=[2, 1], nt=[3, 2],
+                    inflow=infl, tol=1e-6, max_iter=200)
+    np.testing.assert_allclose(gpu["phi"], val, rtol=2e-6)
+
+
+def test_inflow_isotropic_and_per_ordinate_parity(rom):
+    I, J = 33, 27
+    bounds = (0, 1, 0, 1)
+    st, ss, q = W.random_medium(I, J, seed=55)
+    sets = [O.Ordinates(*W.random_directions(9, seed=56, weights="random"))]
+    iso = W.random_inflow(I, J, seed=57)
+    gpu = gpu_solve(rom, I, J, bounds, st, ss, q, sets=sets, inflow=iso, fixed_iters=5)
+    ref = O.solve_xy(I, J, bounds, st, ss, q, sets, inflow=iso, fixed_iters=5)
+    assert rel(gpu["phi"][0], ref["phi"][0]) < TOL
+    per = W.random_inflow(I, J, seed=58, per_ordinate_M=9)
+    gpu = gpu_solve(rom, I, J, bounds, st, ss, q, sets=sets, inflow_ord=per, fixed_iters=5)
+    ref = O.solve_xy(I, J, bounds, st, ss, q, sets, inflow=per, inflow_per_ordinate=True,
+                     fixed_iters=5)
+    assert rel(gpu["phi"][0], ref["phi"][0]) < TOL
+
+
+# ------------------------------------------------------ edges and drivers
+
+def test_zero_source_converges_immediately(rom):
+    I, J = 20, 20
+    gpu = gpu_solve(rom, I, J, (0, 1, 0, 1), 1.0, 0.5, 0.0, seed=3, nz=[1], nt=[1], tol=1e-6)
+    assert np.all(gpu["phi"] == 0.0)
+    assert list(gpu["iters"]) == [1]
+
+
+def test_graph_loop_equals_host_loop(rom):
+    p = W.point_source(n=96, n_samples=6)
+    nz = nt = [2] * 6
+    a = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, seed=5, nz=nz, nt=nt,
+                  tol=1e-6, check_every=0)
+    b = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, seed=5, nz=nz, nt=nt,
+                  tol=1e-6, check_every=1)
+    c = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, seed=5, nz=nz, nt=nt,
+                  tol=1e-6, check_every=7)
+    np.testing.assert_array_equal(a["phi"], b["phi"])
+    np.testing.assert_array_equal(a["phi"], c["phi"])
+    np.testing.assert_array_equal(a["iters"], b["iters"])
+    assert a["stats"]["updates"] == b["stats"]["updates"] > 0
+
+
+def test_device_grid_equals_host_grid(rom):
+    import torch
+    I, J = 50, 41
+    bounds = (0, 2, 0, 1)
+    st, ss, q = W.random_medium(I, J, seed=8)
+    a = gpu_solve(rom, I, J, bounds, st, ss, q, seed=2, nz=[2], nt=[2], fixed_iters=3)
+    ctx = rom.RomContext(0)
+    t = [torch.tensor(x, dtype=torch.float32, device="cuda") for x in (st, ss, q)]
+    ctx.set_grid_device(I, J, bounds, *t)
+    ctx.set_ordinates_seed(2, [2], [2])
+    ctx.set_options(fixed_iters=3)
+    ctx.solve()
+    out = torch.zeros((J, I), dtype=torch.float64, device="cuda")
+    ctx.scalar_flux_device(out, 0)
+    torch.cuda.synchronize()
+    b = out.cpu().numpy()
+    ctx.close()
+    np.testing.assert_array_equal(a["phi"][0], b)
+
+
+def test_invalid_arguments_rejected(rom):
+    ctx = rom.RomContext(0)
+    with pytest.raises(rom.RomError) as e:
+        ctx.set_grid(4, 4, (0, 1, 0, 1), 1.0, 1.0, 0.0)  # sigma_S = sigma_T
+    assert e.value.code == -1
+    with pytest.raises(rom.RomError):
+        ctx.set_grid(4, 4, (0, 1, 0, 1), 1.0, 0.5, -1.0)  # q < 0
+    with pytest.raises(rom.RomError) as e:
+        ctx.solve()
+    assert e.value.code == -6
+    ctx.set_grid(4, 4, (0, 1, 0, 1), 1.0, 0.5, 1.0)
+    with pytest.raises(rom.RomError):
+        ctx.set_ordinates([(np.array([0.9]), np.array([0.9]), np.array([0.1]), np.array([1.0]))])
+    with pytest.raises(rom.RomError) as e:
+        ctx.set_kernel("hg", 0.8)
+    assert e.value.code == -7
+    ctx.close()
+
+
+def test_not_converged_reported(rom):
+    ctx = rom.RomContext(0)
+    p = W.example_2_1(I=30, J=30)
+    ctx.set_grid(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q)
+    ctx.set_ordinates_seed(1, [2], [2])
+    ctx.set_options(tol=1e-12, max_iter=3)
+    with pytest.raises(rom.RomError) as e:
+        ctx.solve()
+    assert e.value.code == -4
+    it, _ = ctx.iterations()
+    assert list(it) == [3]
+    ctx.close()
+
+
+# ----------------------------------------- full-size workload, sampled
+
+def test_point_source_full_size_sampled(rom):
+    """The benchmark workload (256 x 256, 64 ROM samples x 16 ordinates, tol 1e-6,
+    device-side loop) in its benchmark launch configuration; samples 0, 21, 63
+    are solved by the oracle one by one (tol 1e-12)."""
+    p = W.point_source()
+    S = 64
+    seed = W.ordinate_seed(1)
+    nz = nt = [2] * S
+    gpu = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, seed=seed, nz=nz, nt=nt,
+                    tol=1e-6)
+    for k in (0, 21, 63):
+        ref = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q,
+                         [O.rom_ordinates_xy(seed, k, 2, 2)], tol=1e-12)
+        assert rel(gpu["phi"][k], ref["phi"][0]) < TOL, k
+    assert np.all(gpu["resid"] < 1e-6)
+    np.testing.assert_allclose(gpu["avg"], gpu["phi"].astype(np.float64).mean(0), rtol=1e-12)
