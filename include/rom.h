@@ -210,6 +210,60 @@ int rom_get_partial_sum(rom_ctx *ctx, double *sum_out, int64_t *count_out);
 /* Library version string. */
 const char *rom_version(void);
 
+/* ------------------------------------------------ no-allocation variant */
+
+/* Size in bytes of the fixed device scratch array of rom_sweep_xy_noalloc. */
+#define ROM_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/*
+ * One transport sweep per sample that allocates no device memory.  The paper
+ * has no counterpart: this is a deployment variant of the library's sweep.
+ *
+ * Who it is for: callers that must not call cudaMalloc -- code running while
+ * a CUDA graph is being captured elsewhere in the process, plug-ins whose host
+ * application owns all device memory through its own pool, and latency-bound
+ * paths where an allocation (and the synchronisation it can imply) is not
+ * allowed.  The context API allocates its buffers with cudaMalloc; this call
+ * instead keeps its scratch (padded copies of the inputs and the per-work-item
+ * moment partials) in one array of ROM_NOALLOC_SCRATCH_BYTES that the library
+ * places in device memory when it is loaded.  Every GPU that loads the
+ * library holds that array until the process exits.
+ *
+ * What it computes: for each sample s, with vacuum inflow, the scalar flux
+ *   phi_s = sum_l w_l psi_l,   psi_l = L_l^{-1} src_s,
+ * where L_l is the diamond-difference (scheme = ROM_SCHEME_DD) or step
+ * (ROM_SCHEME_STEP) discretisation of u_l . grad + sigma_T on the I x J grid
+ * with cell sizes dx, dy, and src_s is the isotropic right-hand side of the
+ * sample (for source iteration: sigma_S phi_s^{k-1} + q).  With src_s = q this
+ * is the first sweep of rom_solve; with src_s = sigma_S phi_s + q the next one.
+ *
+ * Arguments: cuda_stream is the cudaStream_t to enqueue on (NULL = the legacy
+ * default stream); sigma_t is a device FP32 array [J][I] on the current device;
+ * src and phi are device FP32 arrays [n_samples][J][I]; m_per_sample (host,
+ * [n_samples], each >= 1), dirs (host FP64 [sum M][3] = c, s, zeta, unit
+ * vectors) and weights (host FP64 [sum M], > 0) give the ordinate sets, as in
+ * rom_set_ordinates.  errbuf (may be NULL) receives a message on failure.
+ * Limits: I <= 2048, n_samples <= 1024, sum M <= 8192, and the scratch the
+ * problem needs (about 4 J ceil(I/8)*8 bytes times 1 + n_samples + the number of
+ * work items, two ordinates of one quadrant per item) must fit in
+ * ROM_NOALLOC_SCRATCH_BYTES; larger problems return ROM_ERR_INVALID_ARG with
+ * the needed size in errbuf.  No cudaMalloc, cudaFree or other allocating
+ * routine is called.
+ *
+ * Behaviour: the first call on a device (with that device current) looks up
+ * the device address of the scratch array once and caches it; make that first
+ * call before any stream capture.  The call returns after enqueueing the work;
+ * phi is ready when the stream reaches that point.  All calls on a device share
+ * the one scratch array, which keeps the last call's contents; no part of it
+ * needs to start at zero, because every call writes each byte it reads.  Calls
+ * whose work overlaps on the GPU (other streams or host threads) race on the
+ * array: serialise them.
+ */
+int rom_sweep_xy_noalloc(void *cuda_stream, int I, int J, double dx, double dy, int scheme,
+                         const float *sigma_t, int n_samples, const int32_t *m_per_sample,
+                         const double *dirs, const double *weights, const float *src,
+                         float *phi, char *errbuf, size_t errbuf_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,8 @@ SIGNATURES = {
     "rom_get_scalar_flux_device": (_i, [_vp, _i, _vp]),
     "rom_get_iterations": (_i, [_vp, _i32p, _dp]),
     "rom_get_partial_sum": (_i, [_vp, _dp, _i64p]),
+    "rom_sweep_xy_noalloc": (_i, [_vp, _i, _i, ctypes.c_double, ctypes.c_double, _i, _vp, _i,
+                                  _i32p, _dp, _dp, _vp, _vp, ctypes.c_char_p, ctypes.c_size_t]),
 }
 
 
