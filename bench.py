@@ -174,10 +174,12 @@ def run_reference(args):
         return 0
     for _ in range(args.warmup):
         oracle_rate(0.0, 1)
+    # each step: consecutive samples of the workload for a share of a ~1 minute budget
+    per_step = max(0.02, args.ref_total / max(args.steps, 1))
     t_tot, upd_tot, ns_tot = 0.0, 0, 0
     threads = 1
     for k in range(args.steps):
-        rate, ns, threads, upd, dt = oracle_rate(args.ref_budget, 64, first=1000 * (k + 1))
+        rate, ns, threads, upd, dt = oracle_rate(per_step, 64, first=N_SAMPLES * (k + 1))
         t_tot += dt
         upd_tot += upd
         ns_tot += ns
@@ -190,7 +192,7 @@ def run_reference(args):
         "config": workload_config({"reference": "FP64 CPU oracle (oracle/rom_oracle.c, OpenMP)"}),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{ns_tot} ROM samples of the workload over {args.steps} "
-                                   f"steps (each step <= {args.ref_budget:.0f} s of CPU work)"},
+                                   f"steps (each step about {per_step:.2f} s of CPU work)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -284,15 +286,22 @@ def run_ours(args):
     ctx.set_options(tol=TOL, tile_g=args.tile_g)
     peak_tflops = 152 * 128 * 2 * 2070e6 / 1e12
     achieved = sweep_upd * FLOP_PER_UPDATE / (sweep_ms / 1e3) / 1e12
+    # DRAM bytes of one full sweep launch from the committed ncu capture, used
+    # only while the sweep source is the one that was captured
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "sweep2d_traffic.json")
-    if os.path.exists(tpath):
+    tpath = os.path.join(ROOT, "profiles", "sweep2d_point_source_256x64.traffic.json")
+    spath = os.path.join(ROOT, "paper_2407_12527_gb300", "csrc", "sweep2d.cu")
+    if os.path.exists(tpath) and args.tile_g in (0, 2):
+        import hashlib
         with open(tpath) as f:
             tr = json.load(f)
-        if tr.get("valid_for") == "sweep2d_kernel<G=2,MOM=1,DD,homog> point_source_256 x 64":
-            traffic = tr.get("bytes_per_launch")
+        with open(spath, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+        if tr.get("sweep2d_cu_sha256") == digest:
+            traffic = tr.get("dram_bytes_per_launch")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
+                "traffic_note": "DRAM read+write bytes of one full sweep launch (ncu)",
                 "kernel": "sweep2d_kernel (K1)",
                 "launches": sweep_n, "avg_launch_us": 1e3 * sweep_ms / max(sweep_n, 1),
                 "flop_per_update": FLOP_PER_UPDATE,
@@ -351,8 +360,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--check-every", type=int, default=0,
@@ -363,7 +372,8 @@ def main():
     ap.add_argument("--only-timed", action="store_true",
                     help="run the warm-up and timed steps only (no roofline, e2e or CPU legs)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--ref-budget", type=float, default=8.0)
+    ap.add_argument("--ref-total", type=float, default=60.0,
+                    help="CPU seconds the reference (oracle) arm spends over all its steps")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

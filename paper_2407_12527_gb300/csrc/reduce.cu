@@ -8,7 +8,9 @@
 //           so that the next sweep forms S_l = S0 + c_l S1x + s_l S1y
 //           (eq. equ_random with eq. anisotropic kernel, mirror-averaged in
 //           zeta, where sum_l' w_l' (1 + g u_l'.u_l) psi_l' = phi + g (c Jx + s Jy)),
-//           and per-block FP64 partial sums of |phi^k - phi^{k-1}|^2 and |phi^k|^2.
+//           and per-block FP64 partial sums of |phi^k - phi^{k-1}|^2 and |phi^k|^2
+//           (each thread first sums the squares of its few cells in FP32; the
+//           FP64 units of GB300 are few, so FP64 is used from the warp sums on).
 // finalize: relative l2 change per sample (Sec. 3.2 source iteration stopping
 //           rule of this library), sweep counters, the active flags, and the
 //           number of samples still iterating (optionally the condition of the
@@ -39,54 +41,77 @@ __global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
     const int s = blockIdx.y;
     if (!A.active[s]) return;
     const int ib = A.item_begin[s], ie = A.item_begin[s + 1];
-    const float4 *part = reinterpret_cast<const float4 *>(A.part);
-    float4 *phi = reinterpret_cast<float4 *>(A.phi) + (long long)s * MOM * A.cells4;
-    float4 *src = reinterpret_cast<float4 *>(A.src) + (long long)s * MOM * A.cells4;
-    const float4 *sig_s = reinterpret_cast<const float4 *>(A.sigma_s);
-    const float4 *q = reinterpret_cast<const float4 *>(A.q);
-    double d2 = 0.0, n2 = 0.0;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < A.cells4;
-         v += (long long)gridDim.x * blockDim.x) {
-        float4 acc[MOM];
+    const long long cells = A.cells;  // a multiple of 8: every thread owns one 32-byte sector
+    float *phi = A.phi + (long long)s * MOM * cells;
+    float *src = A.src + (long long)s * MOM * cells;
+    float d2f = 0.f, n2f = 0.f;
+    for (long long v = 8 * ((long long)blockIdx.x * blockDim.x + threadIdx.x); v < cells;
+         v += 8LL * gridDim.x * blockDim.x) {
+        float acc[MOM][8];
 #pragma unroll
-        for (int m = 0; m < MOM; ++m) acc[m] = make_float4(0.f, 0.f, 0.f, 0.f);
-        // items in batches of four independent loads, summed in item order
+        for (int m = 0; m < MOM; ++m)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc[m][e] = 0.f;
+        float old[8], ss[8], qq[8], out[8];
+        ld8_volatile(phi + v, old);
+        ldg8(A.sigma_s + v, ss);
+        ldg8(A.q + v, qq);
+        // items in batches of eight independent loads, summed in item order
         int it = ib;
+        for (; it + 8 <= ie; it += 8)
+#pragma unroll
+            for (int m = 0; m < MOM; ++m) {
+                float t[8][8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) ldg8(A.part + ((long long)(it + u) * MOM + m) * cells + v, t[u]);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc[m][e] += t[u][e];
+            }
         for (; it + 4 <= ie; it += 4)
 #pragma unroll
             for (int m = 0; m < MOM; ++m) {
-                float4 t[4];
+                float t[4][8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) t[u] = part[((long long)(it + u) * MOM + m) * A.cells4 + v];
+                for (int u = 0; u < 4; ++u) ldg8(A.part + ((long long)(it + u) * MOM + m) * cells + v, t[u]);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) acc[m] = add4(acc[m], t[u]);
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc[m][e] += t[u][e];
             }
         for (; it < ie; ++it)
 #pragma unroll
-            for (int m = 0; m < MOM; ++m)
-                acc[m] = add4(acc[m], part[((long long)it * MOM + m) * A.cells4 + v]);
-        const float4 old = phi[v];
-        const double dx = (double)acc[0].x - old.x, dy = (double)acc[0].y - old.y;
-        const double dz = (double)acc[0].z - old.z, dw = (double)acc[0].w - old.w;
-        d2 += dx * dx + dy * dy + dz * dz + dw * dw;
-        n2 += (double)acc[0].x * acc[0].x + (double)acc[0].y * acc[0].y +
-              (double)acc[0].z * acc[0].z + (double)acc[0].w * acc[0].w;
+            for (int m = 0; m < MOM; ++m) {
+                float t[8];
+                ldg8(A.part + ((long long)it * MOM + m) * cells + v, t);
 #pragma unroll
-        for (int m = 0; m < MOM; ++m) phi[m * A.cells4 + v] = acc[m];
-        const float4 ss = sig_s[v], qq = q[v];
-        src[v] = make_float4(fmaf(ss.x, acc[0].x, qq.x), fmaf(ss.y, acc[0].y, qq.y),
-                             fmaf(ss.z, acc[0].z, qq.z), fmaf(ss.w, acc[0].w, qq.w));
+                for (int e = 0; e < 8; ++e) acc[m][e] += t[e];
+            }
+        // per-element squares in FP32 (a few terms per thread), norms in FP64 below
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const float dd = acc[0][e] - old[e];
+            d2f = fmaf(dd, dd, d2f);
+            n2f = fmaf(acc[0][e], acc[0][e], n2f);
+        }
+#pragma unroll
+        for (int m = 0; m < MOM; ++m) stg8(phi + m * cells + v, acc[m]);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) out[e] = fmaf(ss[e], acc[0][e], qq[e]);
+        stg8(src + v, out);
         if (MOM == 3) {
-            const float g = A.g;
 #pragma unroll
-            for (int m = 1; m < 3; ++m)
-                src[m * A.cells4 + v] = make_float4(g * ss.x * acc[m].x, g * ss.y * acc[m].y,
-                                                    g * ss.z * acc[m].z, g * ss.w * acc[m].w);
+            for (int m = 1; m < 3; ++m) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) out[e] = A.g * ss[e] * acc[m][e];
+                stg8(src + m * cells + v, out);
+            }
         }
     }
     __shared__ double red[2][32];
-    d2 = warp_sum(d2);
-    n2 = warp_sum(n2);
+    double d2 = warp_sum((double)d2f);
+    double n2 = warp_sum((double)n2f);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) {
         red[0][w] = d2;

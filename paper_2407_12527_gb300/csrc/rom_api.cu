@@ -890,8 +890,8 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
         if ((rc = upload_inflow(ctx))) return rc;
         invalidate_graph(ctx);
     }
-    // residual chunks: blocks of 256 threads with two float4 of cells each
-    const int chunks = (int)std::max<long long>(1, (cells / 4 + 511) / 512);
+    // residual chunks: blocks of 256 threads with one 8-cell sector each
+    const int chunks = (int)std::max<long long>(1, (cells / 8 + 255) / 256);
     if (chunks != ctx->chunks) invalidate_graph(ctx);
     ctx->chunks = chunks;
     const int MOM = ctx->MOM;

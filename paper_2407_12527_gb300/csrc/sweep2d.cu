@@ -21,32 +21,83 @@
 // in registers across steps.  Each cell is visited once per ordinate group:
 // source loads and moment stores are full sectors, and the G ordinates and the
 // H x 8 block give the instruction-level parallelism that hides the
-// FMA -> MUL -> FMA chain of each cell.  No ordinate or cell values are
-// stored: only the moments of each item, which a later kernel sums per sample.
+// FMA -> MUL -> FMA chain of each cell.  Ordinates are processed in pairs with
+// the packed FP32x2 instructions of sm_100+ (__ffma2_rn, __fmul2_rn), which
+// halves the issue slots of the cell arithmetic.  The source rows of the next
+// block are loaded one step ahead into registers.  No ordinate or cell values
+// are stored: only the moments of each item, which a later kernel sums per
+// sample.
 #include "rom_internal.cuh"
 
 namespace romk {
 namespace {
 
-constexpr int kH = 4;  // rows per lane per wavefront step
+constexpr int kH = 4;        // rows per lane per wavefront step
+constexpr int kPrefetch = 1;  // steps between the load of a block's rows and their use
 
-__device__ __forceinline__ void ld8(const float *__restrict__ p, float (&v)[kCols])
-{
-    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
-    const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-}
-
-__device__ __forceinline__ void st8(float *__restrict__ p, const float (&v)[kCols])
-{
-    reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
-    reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
-}
-
+// ---- packs: one ordinate (float), or two ordinates (float2, FP32x2 ops)
 template <int G>
-struct OrdRegs {
-    float a[G], b[G], w[G], rd[G], c[G], s[G], wc[G], ws[G];
+struct Pack {
+    using T = float2;
+    static constexpr int N = G / 2;
+};
+template <>
+struct Pack<1> {
+    using T = float;
+    static constexpr int N = 1;
+};
+
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 fma_(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float2 mul_(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float2 add_(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float neg_(float a) { return -a; }
+__device__ __forceinline__ float2 neg_(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ float2 rcp_(float2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+__device__ __forceinline__ float hsum(float a) { return a; }
+__device__ __forceinline__ float hsum(float2 a) { return a.x + a.y; }
+__device__ __forceinline__ void setc(float &a, int, float v) { a = v; }
+__device__ __forceinline__ void setc(float2 &a, int i, float v)
+{
+    if (i) a.y = v;
+    else a.x = v;
+}
+template <class T>
+__device__ __forceinline__ T splat(float s);
+template <>
+__device__ __forceinline__ float splat<float>(float s) { return s; }
+template <>
+__device__ __forceinline__ float2 splat<float2>(float s) { return make_float2(s, s); }
+
+template <bool DOWN>
+__device__ __forceinline__ float shfl1(float v)
+{
+    return DOWN ? __shfl_down_sync(0xffffffffu, v, 1) : __shfl_up_sync(0xffffffffu, v, 1);
+}
+template <bool DOWN>
+__device__ __forceinline__ float2 shfl1(float2 v)
+{
+    return make_float2(shfl1<DOWN>(v.x), shfl1<DOWN>(v.y));
+}
+
+__device__ __forceinline__ void ld8(const float *__restrict__ p, float (&v)[kCols]) { ldg8_early(p, v); }
+__device__ __forceinline__ void st8(float *__restrict__ p, const float (&v)[kCols]) { stg8(p, v); }
+
+// Per-ordinate constants of a work item, grouped in packs.
+template <int G>
+struct OrdPacks {
+    using T = typename Pack<G>::T;
+    static constexpr int N = Pack<G>::N;
+    T a[N], b[N], ab[N], w[N], rd[N], c[N], s[N], wc[N], ws[N];
+    // uniform sigma_T: the cell update folded into one FMA per upwind chain
+    //   DD:   x_out  = al x + 2rd (S + b py),   al = 2a rd - 1
+    //         py_out = a2 x + 2rd S + be py,    a2 = 2a rd, be = 2b rd - 1
+    //         psi_c  = (x + x_out) / 2
+    //   step: psi_c  = ar x + rd (S + b py) = x_out = py_out,  ar = a rd, br = b rd
+    T al[N], a2[N], b2[N], be[N], r2[N], wh[N], ar[N], br[N];
     int ord[G];
 };
 
@@ -57,17 +108,27 @@ struct RowBuf {
     float v[NA][kH][kCols];
 };
 
+// Offset of row h of block blk for the lane's columns: base + h * rs.
+struct RowAddr {
+    long long base, rs;
+    __device__ __forceinline__ RowAddr(const SweepArgs &A, int blk, bool yneg, int col0)
+    {
+        const int jl0 = blk * kH;
+        base = (long long)(yneg ? (A.J - 1 - jl0) : jl0) * A.NXP + col0;
+        rs = yneg ? -(long long)A.NXP : (long long)A.NXP;
+    }
+};
+
 // Issue the loads of the rows of block `blk` (rows past J are skipped).
 template <int MOM, bool HOMOG>
 __device__ __forceinline__ void load_block(const SweepArgs &A, int blk, bool yneg, int col0,
                                            const float *__restrict__ src_s, RowBuf<MOM, HOMOG> &b)
 {
+    const RowAddr ra(A, blk, yneg, col0);
 #pragma unroll
     for (int h = 0; h < kH; ++h) {
-        const int jl = blk * kH + h;
-        if (jl < A.J) {
-            const int j = yneg ? (A.J - 1 - jl) : jl;
-            const long long row = (long long)j * A.NXP + col0;
+        if (blk * kH + h < A.J) {
+            const long long row = ra.base + h * ra.rs;
 #pragma unroll
             for (int m = 0; m < MOM; ++m) ld8(src_s + m * A.cells + row, b.v[m][h]);
             if (!HOMOG) ld8(A.sigma_t + row, b.v[MOM][h]);
@@ -76,73 +137,129 @@ __device__ __forceinline__ void load_block(const SweepArgs &A, int blk, bool yne
 }
 
 // One H x 8 block of cells for all G ordinates of the item, from the rows in b.
-template <int G, int MOM, int SCHEME, bool HOMOG, bool XNEG, bool CHECK>
+// The block's moments are left in out[][][] (LATE: the caller stores them
+// after the shuffle), or stored row by row at part_i (three moments: the
+// registers for holding them are not there).
+template <int G, int MOM, int SCHEME, bool HOMOG, bool XNEG, bool CHECK, bool LATE>
 __device__ __forceinline__ void sweep_block(const SweepArgs &A, int blk, bool yneg, int col0,
-                                            const OrdRegs<G> &o, float (&py)[kCols][G],
-                                            const float (&xin)[kH][G], float (&xo)[kH][G],
+                                            const OrdPacks<G> &o,
+                                            typename Pack<G>::T (&py)[kCols][Pack<G>::N],
+                                            const typename Pack<G>::T (&xin)[kH][Pack<G>::N],
+                                            typename Pack<G>::T (&xo)[kH][Pack<G>::N],
                                             const RowBuf<MOM, HOMOG> &b,
+                                            float (&out)[LATE ? MOM : 1][kH][kCols],
                                             float *__restrict__ part_i)
 {
+    using T = typename Pack<G>::T;
+    constexpr int N = Pack<G>::N;
+    const T two = splat<T>(2.f);
 #pragma unroll
     for (int h = 0; h < kH; ++h) {
-        const int jl = blk * kH + h;
-        if (CHECK && jl >= A.J) {
+        if (CHECK && blk * kH + h >= A.J) {
 #pragma unroll
-            for (int k = 0; k < G; ++k) xo[h][k] = 0.f;
+            for (int p = 0; p < N; ++p) xo[h][p] = splat<T>(0.f);
             continue;
         }
-        const int j = yneg ? (A.J - 1 - jl) : jl;
-        const long long row = (long long)j * A.NXP + col0;
-        float x[G];
+        T x[N];
 #pragma unroll
-        for (int k = 0; k < G; ++k) x[k] = xin[h][k];
-        float p0[kCols], p1[kCols], p2[kCols];
+        for (int p = 0; p < N; ++p) x[p] = xin[h][p];
+        T acc0[kCols], acc1[kCols], acc2[kCols];
 #pragma unroll
-        for (int r = 0; r < kCols; ++r) p0[r] = p1[r] = p2[r] = 0.f;
+        for (int r = 0; r < kCols; ++r) acc0[r] = acc1[r] = acc2[r] = splat<T>(0.f);
 #pragma unroll
         for (int rr = 0; rr < kCols; ++rr) {
             const int r = XNEG ? (kCols - 1 - rr) : rr;
             const bool ok = !CHECK || (col0 + r < A.I);
+            const T s0 = splat<T>(b.v[0][h][r]);
 #pragma unroll
-            for (int k = 0; k < G; ++k) {
-                float S = b.v[0][h][r];
-                if (MOM == 3) S = fmaf(o.c[k], b.v[1][h][r], fmaf(o.s[k], b.v[2][h][r], S));
-                const float num = fmaf(o.a[k], x[k], fmaf(o.b[k], py[r][k], S));
-                const float rden =
-                    HOMOG ? o.rd[k]
-                          : __frcp_rn(b.v[RowBuf<MOM, HOMOG>::NA - 1][h][r] + o.a[k] + o.b[k]);
-                const float pc = num * rden;
-                if (ok) {
-                    if (SCHEME == 0) {
-                        x[k] = fmaf(2.f, pc, -x[k]);
-                        py[r][k] = fmaf(2.f, pc, -py[r][k]);
-                    } else {
-                        x[k] = pc;
-                        py[r][k] = pc;
+            for (int p = 0; p < N; ++p) {
+                T S = s0;
+                if (MOM == 3)
+                    S = fma_(o.c[p], splat<T>(b.v[1][h][r]), fma_(o.s[p], splat<T>(b.v[2][h][r]), S));
+                if (HOMOG && SCHEME == 0) {
+                    const T s2 = mul_(S, o.r2[p]);                 // 2 rd S
+                    const T xn = fma_(o.al[p], x[p], fma_(o.b2[p], py[r][p], s2));
+                    const T pyn = fma_(o.a2[p], x[p], fma_(o.be[p], py[r][p], s2));
+                    if (ok) {
+                        acc0[r] = fma_(o.wh[p], add_(x[p], xn), acc0[r]);
+                        if (MOM == 3) {
+                            const T sm = add_(x[p], xn);
+                            acc1[r] = fma_(mul_(o.wc[p], splat<T>(0.5f)), sm, acc1[r]);
+                            acc2[r] = fma_(mul_(o.ws[p], splat<T>(0.5f)), sm, acc2[r]);
+                        }
+                        x[p] = xn;
+                        py[r][p] = pyn;
                     }
-                    p0[r] = fmaf(o.w[k], pc, p0[r]);
-                    if (MOM == 3) {
-                        p1[r] = fmaf(o.wc[k], pc, p1[r]);
-                        p2[r] = fmaf(o.ws[k], pc, p2[r]);
+                } else if (HOMOG) {
+                    const T pc = fma_(o.ar[p], x[p], fma_(o.br[p], py[r][p], mul_(S, o.rd[p])));
+                    if (ok) {
+                        x[p] = pc;
+                        py[r][p] = pc;
+                        acc0[r] = fma_(o.w[p], pc, acc0[r]);
+                        if (MOM == 3) {
+                            acc1[r] = fma_(o.wc[p], pc, acc1[r]);
+                            acc2[r] = fma_(o.ws[p], pc, acc2[r]);
+                        }
+                    }
+                } else {
+                    const T num = fma_(o.a[p], x[p], fma_(o.b[p], py[r][p], S));
+                    const T rden =
+                        rcp_(add_(splat<T>(b.v[RowBuf<MOM, HOMOG>::NA - 1][h][r]), o.ab[p]));
+                    const T pc = mul_(num, rden);
+                    if (ok) {
+                        if (SCHEME == 0) {
+                            x[p] = fma_(two, pc, neg_(x[p]));
+                            py[r][p] = fma_(two, pc, neg_(py[r][p]));
+                        } else {
+                            x[p] = pc;
+                            py[r][p] = pc;
+                        }
+                        acc0[r] = fma_(o.w[p], pc, acc0[r]);
+                        if (MOM == 3) {
+                            acc1[r] = fma_(o.wc[p], pc, acc1[r]);
+                            acc2[r] = fma_(o.ws[p], pc, acc2[r]);
+                        }
                     }
                 }
             }
         }
 #pragma unroll
-        for (int k = 0; k < G; ++k) xo[h][k] = x[k];
-        st8(part_i + row, p0);
-        if (MOM == 3) {
-            st8(part_i + A.cells + row, p1);
-            st8(part_i + 2 * A.cells + row, p2);
+        for (int p = 0; p < N; ++p) xo[h][p] = x[p];
+        if constexpr (LATE) {
+#pragma unroll
+            for (int r = 0; r < kCols; ++r) out[0][h][r] = hsum(acc0[r]);
+            if constexpr (MOM == 3) {
+#pragma unroll
+                for (int r = 0; r < kCols; ++r) {
+                    out[MOM - 2][h][r] = hsum(acc1[r]);
+                    out[MOM - 1][h][r] = hsum(acc2[r]);
+                }
+            }
+        } else {
+            const RowAddr ra(A, blk, yneg, col0);
+            float v[kCols];
+#pragma unroll
+            for (int r = 0; r < kCols; ++r) v[r] = hsum(acc0[r]);
+            st8(part_i + ra.base + h * ra.rs, v);
+            if (MOM == 3) {
+#pragma unroll
+                for (int r = 0; r < kCols; ++r) v[r] = hsum(acc1[r]);
+                st8(part_i + A.cells + ra.base + h * ra.rs, v);
+#pragma unroll
+                for (int r = 0; r < kCols; ++r) v[r] = hsum(acc2[r]);
+                st8(part_i + 2 * A.cells + ra.base + h * ra.rs, v);
+            }
         }
     }
 }
 
 template <int G, int MOM, int SCHEME, bool HOMOG, bool XNEG>
 __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &it,
-                                           const OrdRegs<G> &o)
+                                           const OrdPacks<G> &o)
 {
-    __shared__ float xbuf[2][kMaxWarps][kH][G];
+    using T = typename Pack<G>::T;
+    constexpr int N = Pack<G>::N;
+    __shared__ T xbuf[2][kMaxWarps][kH][N];
     const int g = threadIdx.x;
     const int nwarps = blockDim.x >> 5;
     const int L = (A.I + kCols - 1) / kCols;  // lanes that own cells
@@ -151,11 +268,11 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
     const int col0 = g * kCols;
     const bool yneg = (it.quad >> 1) & 1;
     const int nblk = (A.J + kH - 1) / kH;
-    const int T = nblk + L - 1;
+    const int T_steps = nblk + L - 1;
     const bool full_cols = col0 + kCols <= A.I;
 
     // incoming y-edge values of the lane's columns (face y_B, or y_T when s < 0)
-    float py[kCols][G];
+    T py[kCols][N];
 #pragma unroll
     for (int r = 0; r < kCols; ++r)
 #pragma unroll
@@ -164,30 +281,38 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
             if (A.inflow && lane_on && col0 + r < A.I && k < it.n)
                 v = A.inflow[(long long)o.ord[k] * A.inflow_stride + 2 * A.J + (yneg ? A.I : 0) +
                              col0 + r];
-            py[r][k] = v;
+            setc(py[r][G == 1 ? 0 : k >> 1], G == 1 ? 0 : k & 1, v);
         }
 
-    float xin[kH][G];
+    T xin[kH][N];
 #pragma unroll
     for (int h = 0; h < kH; ++h)
 #pragma unroll
-        for (int k = 0; k < G; ++k) xin[h][k] = 0.f;
+        for (int p = 0; p < N; ++p) xin[h][p] = splat<T>(0.f);
 
     const float *src_s = A.src + (long long)it.sample * MOM * A.cells;
     float *part_i = A.part + (long long)blockIdx.x * MOM * A.cells;
 
-    // Rows of the lane's next block are loaded one step ahead (two register
-    // buffers used in turn), so their latency overlaps the current block.  With
-    // more than two arrays per cell (linear kernel) the registers are not
-    // there; the rows are then loaded at the start of their step.
-    constexpr bool PF = RowBuf<MOM, HOMOG>::NA <= 2;
-    RowBuf<MOM, HOMOG> buf0, buf1;
+    // The rows of the lane's block for step t + PD are loaded at the start of
+    // step t into a ring of PD + 1 register buffers indexed by t (the same index
+    // for every lane: lane d at step t works on block t - d).  With more than
+    // two arrays per cell (linear kernel) the registers are not there; the rows
+    // are then loaded at the start of their step.
+    constexpr int NA = RowBuf<MOM, HOMOG>::NA;
+    constexpr bool PF = NA <= 2;
+    constexpr int PD = NA == 1 ? kPrefetch : (NA == 2 ? 1 : 0);
+    // moments are stored row by row inside the block (holding a whole block's
+    // moments until the end of the step measured slower on GB300)
+    constexpr bool STORE_LATE = false;
+    RowBuf<MOM, HOMOG> buf[PD + 1];
     auto step = [&](int t, RowBuf<MOM, HOMOG> &cur, RowBuf<MOM, HOMOG> &nxt) {
         const int blk = t - d;
-        if (PF && lane_on && blk + 1 >= 0 && blk + 1 < nblk)
-            load_block<MOM, HOMOG>(A, blk + 1, yneg, col0, src_s, nxt);
-        float xo[kH][G];
-        if (lane_on && blk >= 0 && blk < nblk) {
+        const bool active = lane_on && blk >= 0 && blk < nblk;
+        if (PF && lane_on && blk + PD >= 0 && blk + PD < nblk)
+            load_block<MOM, HOMOG>(A, blk + PD, yneg, col0, src_s, nxt);
+        T xo[kH][N];
+        float out[STORE_LATE ? MOM : 1][kH][kCols];
+        if (active) {
             if (!PF) load_block<MOM, HOMOG>(A, blk, yneg, col0, src_s, cur);
             if (d == 0) {  // incoming x-edge values (face x_L, or x_R when c < 0)
 #pragma unroll
@@ -201,28 +326,37 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
                             v = A.inflow[(long long)o.ord[k] * A.inflow_stride + (XNEG ? A.J : 0) +
                                          j];
                         }
-                        xin[h][k] = v;
+                        setc(xin[h][G == 1 ? 0 : k >> 1], G == 1 ? 0 : k & 1, v);
                     }
             }
-            if (full_cols && (blk + 1) * kH <= A.J)
-                sweep_block<G, MOM, SCHEME, HOMOG, XNEG, false>(A, blk, yneg, col0, o, py, xin, xo,
-                                                                 cur, part_i);
+            const bool full = full_cols && (blk + 1) * kH <= A.J;
+            if (full)
+                sweep_block<G, MOM, SCHEME, HOMOG, XNEG, false, STORE_LATE>(
+                    A, blk, yneg, col0, o, py, xin, xo, cur, out, part_i);
             else
-                sweep_block<G, MOM, SCHEME, HOMOG, XNEG, true>(A, blk, yneg, col0, o, py, xin, xo,
-                                                                cur, part_i);
+                sweep_block<G, MOM, SCHEME, HOMOG, XNEG, true, STORE_LATE>(
+                    A, blk, yneg, col0, o, py, xin, xo, cur, out, part_i);
         } else {
 #pragma unroll
             for (int h = 0; h < kH; ++h)
 #pragma unroll
-                for (int k = 0; k < G; ++k) xo[h][k] = 0.f;
+                for (int p = 0; p < N; ++p) xo[h][p] = splat<T>(0.f);
         }
         // hand the outgoing x-edge values to the downstream lane
 #pragma unroll
         for (int h = 0; h < kH; ++h)
 #pragma unroll
-            for (int k = 0; k < G; ++k)
-                xin[h][k] = XNEG ? __shfl_down_sync(0xffffffffu, xo[h][k], 1)
-                                 : __shfl_up_sync(0xffffffffu, xo[h][k], 1);
+            for (int p = 0; p < N; ++p) xin[h][p] = shfl1<XNEG>(xo[h][p]);
+        // the step's moments to global memory (when not stored row by row)
+        if (STORE_LATE && active) {
+            const RowAddr ra(A, blk, yneg, col0);
+#pragma unroll
+            for (int h = 0; h < kH; ++h)
+                if (blk * kH + h < A.J)
+#pragma unroll
+                    for (int m = 0; m < (STORE_LATE ? MOM : 1); ++m)
+                        st8(part_i + m * A.cells + ra.base + h * ra.rs, out[m][h]);
+        }
         if (nwarps > 1) {
             const int lane = g & 31, w = g >> 5;
             const bool sender = XNEG ? (lane == 0 && w > 0) : (lane == 31 && w + 1 < nwarps);
@@ -230,7 +364,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
 #pragma unroll
                 for (int h = 0; h < kH; ++h)
 #pragma unroll
-                    for (int k = 0; k < G; ++k) xbuf[t & 1][w][h][k] = xo[h][k];
+                    for (int p = 0; p < N; ++p) xbuf[t & 1][w][h][p] = xo[h][p];
             }
             __syncthreads();
             const bool recv = XNEG ? (lane == 31 && w + 1 < nwarps) : (lane == 0 && w > 0);
@@ -239,20 +373,26 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
 #pragma unroll
                 for (int h = 0; h < kH; ++h)
 #pragma unroll
-                    for (int k = 0; k < G; ++k) xin[h][k] = xbuf[t & 1][src_w][h][k];
+                    for (int p = 0; p < N; ++p) xin[h][p] = xbuf[t & 1][src_w][h][p];
             }
         }
     };
-    if (PF) {
-        if (lane_on && d == 0) load_block<MOM, HOMOG>(A, 0, yneg, col0, src_s, buf0);
+    if constexpr (PF) {
+        // blocks of steps 0 .. PD-1 (buffer k holds the block of step k)
+#pragma unroll
+        for (int k = 0; k < PD; ++k)
+            if (lane_on && k - d >= 0 && k - d < nblk)
+                load_block<MOM, HOMOG>(A, k - d, yneg, col0, src_s, buf[k]);
         int t = 0;
-        for (; t + 1 < T; t += 2) {
-            step(t, buf0, buf1);
-            step(t + 1, buf1, buf0);
+        for (; t + PD < T_steps; t += PD + 1) {
+#pragma unroll
+            for (int k = 0; k <= PD; ++k) step(t + k, buf[k], buf[(k + PD) % (PD + 1)]);
         }
-        if (t < T) step(t, buf0, buf1);
+#pragma unroll
+        for (int k = 0; k < PD; ++k)
+            if (t + k < T_steps) step(t + k, buf[k], buf[(k + PD) % (PD + 1)]);
     } else {
-        for (int t = 0; t < T; ++t) step(t, buf0, buf0);
+        for (int t = 0; t < T_steps; ++t) step(t, buf[0], buf[0]);
     }
 }
 
@@ -261,7 +401,7 @@ __global__ void __launch_bounds__(32 * kMaxWarps) sweep2d_kernel(const SweepArgs
 {
     const SweepItem it = A.items[blockIdx.x];
     if (!A.active[it.sample]) return;
-    OrdRegs<G> o;
+    OrdPacks<G> o;
     const float f = SCHEME == 0 ? 2.f : 1.f;
 #pragma unroll
     for (int k = 0; k < G; ++k) {
@@ -274,14 +414,26 @@ __global__ void __launch_bounds__(32 * kMaxWarps) sweep2d_kernel(const SweepArgs
             w = A.ow[ord];
         }
         o.ord[k] = ord;
-        o.a[k] = f * fabsf(c) * A.inv_dx;
-        o.b[k] = f * fabsf(s) * A.inv_dy;
-        o.w[k] = w;
-        o.rd[k] = HOMOG ? 1.f / (A.sigma_t_homog + o.a[k] + o.b[k]) : 0.f;
-        o.c[k] = c;
-        o.s[k] = s;
-        o.wc[k] = w * c;
-        o.ws[k] = w * s;
+        const float a = f * fabsf(c) * A.inv_dx, b = f * fabsf(s) * A.inv_dy;
+        const int p = G == 1 ? 0 : k >> 1, i = G == 1 ? 0 : k & 1;
+        setc(o.a[p], i, a);
+        setc(o.b[p], i, b);
+        setc(o.ab[p], i, a + b);
+        setc(o.w[p], i, w);
+        setc(o.rd[p], i, HOMOG ? 1.f / (A.sigma_t_homog + a + b) : 0.f);
+        setc(o.c[p], i, c);
+        setc(o.s[p], i, s);
+        setc(o.wc[p], i, w * c);
+        setc(o.ws[p], i, w * s);
+        const float rd = 1.f / (A.sigma_t_homog + a + b);
+        setc(o.al[p], i, (a - b - A.sigma_t_homog) * rd);
+        setc(o.a2[p], i, 2.f * a * rd);
+        setc(o.b2[p], i, 2.f * b * rd);
+        setc(o.be[p], i, (b - a - A.sigma_t_homog) * rd);
+        setc(o.r2[p], i, 2.f * rd);
+        setc(o.wh[p], i, 0.5f * w);
+        setc(o.ar[p], i, a * rd);
+        setc(o.br[p], i, b * rd);
     }
     if (it.quad & 1)
         sweep_item<G, MOM, SCHEME, HOMOG, true>(A, it, o);
