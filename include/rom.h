@@ -84,6 +84,9 @@ typedef struct rom_options {
     int time_kernels;/* 0; 1 records CUDA events around every sweep launch (host-driven     */
                      /* loop, check_every >= 1 is then used, 1 if it is 0) and reports the  */
                      /* summed sweep-kernel time in rom_stats.sweep_ms                     */
+    int dense_source;/* 0: the scattering source from angular moments when the kernel has  */
+                     /* them (isotropic; linear without flags), else from the dense        */
+                     /* M x M operator; 1: always the dense operator                       */
 } rom_options;
 
 /* Statistics of the last rom_solve. */
@@ -181,7 +184,11 @@ int rom_quadrature_xy(int kind, int n1, int n2, double *dirs, double *weights, i
 int rom_get_ordinates(rom_ctx *ctx, double *dirs, double *weights);
 
 /* Scattering kernel P (Sec. 1; eq. anisotropic kernel; eq. wl): kind
- * ROM_KERNEL_*, asymmetry g in (-1, 1), flags ROM_KERNEL_FLAG_*.  Default ISO. */
+ * ROM_KERNEL_*, asymmetry g in (-1, 1), flags ROM_KERNEL_FLAG_*.  Default ISO.
+ * The isotropic and the (mirror-averaged, unnormalised) linear kernel use the
+ * angular moments phi (and Jx, Jy); every other choice uses the dense operator
+ * A[l][l'] = w_l' P(u_l', u_l) of each sample (eq. wl), which stores psi of every
+ * ordinate: 8 bytes per cell and ordinate of device memory. */
 int rom_set_kernel(rom_ctx *ctx, int kind, double g, int flags);
 
 /* ------------------------------------------------------------------ solve */

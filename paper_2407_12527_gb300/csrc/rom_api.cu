@@ -87,8 +87,12 @@ struct rom_ctx {
     std::vector<int> item_begin;
     DevBuf items_dev, item_begin_dev;
 
+    // dense scattering operator (mode 0)
+    DevBuf psi, src_ord, Amat, dtab;
+    bool pmat_dirty = true;
+
     // iteration state
-    int MOM = 1;
+    int MOM = 1;  // 1 isotropic moments, 3 linear moments, 0 dense operator
     int chunks = 1;
     DevBuf phi, src, part, partials, active, iters, flags, resid, n_active, avg, sum, tmp;
     bool solved = false;
@@ -165,6 +169,7 @@ void invalidate_graph(rom_ctx *ctx)
 
 void reset_ordinate_dependents(rom_ctx *ctx)
 {
+    ctx->pmat_dirty = true;
     for (int f = 0; f < 4; ++f) ctx->inflow_ord[f].clear();
     ctx->inflow_dirty = true;
     ctx->items_dirty = true;
@@ -221,11 +226,23 @@ int set_grid_common(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3
     return ROM_OK;
 }
 
+// 1: isotropic moment, 3: linear-kernel moments, 0: dense operator
+int source_mode(const rom_ctx *ctx)
+{
+    if (ctx->opt.dense_source) return 0;
+    if (ctx->kernel_kind == ROM_KERNEL_ISO) return 1;
+    if (ctx->kernel_kind == ROM_KERNEL_LINEAR && ctx->kernel_flags == 0) return 3;
+    return 0;
+}
+
 int choose_g(const rom_ctx *ctx)
 {
-    if (ctx->opt.tile_g == 1 || ctx->opt.tile_g == 2 || ctx->opt.tile_g == 4) return ctx->opt.tile_g;
+    const int cap = source_mode(ctx) == 0 ? 2 : 4;  // dense mode: registers for 2 ordinates
+    if (ctx->opt.tile_g == 1 || ctx->opt.tile_g == 2 || ctx->opt.tile_g == 4)
+        return std::min(ctx->opt.tile_g, cap);
     // largest G that still gives at least two work items per SM
     for (int G : {4, 2}) {
+        if (G > cap) continue;
         long long n = 0;
         for (int s = 0; s < ctx->S; ++s) n += 4 * ((ctx->M[s] / 4 + G - 1) / G);
         if (n >= 2LL * ctx->sm_count) return G;
@@ -339,10 +356,101 @@ romk::SweepArgs sweep_args(const rom_ctx *ctx)
     a.inflow_stride = ctx->inflow_stride;
     a.active = (const int *)ctx->active.p;
     a.cells = (long long)ctx->J * ctx->NXP;
+    if (ctx->MOM == 0) {
+        a.src = (const float *)ctx->src_ord.p;
+        a.psi = (float *)ctx->psi.p;
+    }
     return a;
 }
 
-// One source-iteration sweep: K1 + K2 + K5.
+int max_m(const rom_ctx *ctx)
+{
+    int m = 0;
+    for (int v : ctx->M) m = std::max(m, v);
+    return m;
+}
+
+// device tables of the dense operator: M [S] int, ord_off [S], a_off [S] (long long)
+struct DenseTab {
+    const int *M;
+    const long long *ord_off, *a_off;
+};
+
+DenseTab dense_tab(const rom_ctx *ctx)
+{
+    const unsigned char *b = (const unsigned char *)ctx->dtab.p;
+    const size_t S = ctx->S;
+    DenseTab t;
+    t.ord_off = (const long long *)b;
+    t.a_off = (const long long *)(b + S * 8);
+    t.M = (const int *)(b + S * 16);
+    return t;
+}
+
+romk::DenseArgs dense_args(const rom_ctx *ctx)
+{
+    const DenseTab t = dense_tab(ctx);
+    romk::DenseArgs d{};
+    d.S = ctx->S;
+    d.M = t.M;
+    d.ord_off = t.ord_off;
+    d.a_off = t.a_off;
+    d.A = (const float *)ctx->Amat.p;
+    d.psi = (const float *)ctx->psi.p;
+    d.src = (float *)ctx->src_ord.p;
+    d.sigma_s = (const float *)ctx->sigs.p;
+    d.q = (const float *)ctx->q.p;
+    d.cells = (long long)ctx->J * ctx->NXP;
+    d.active = (const int *)ctx->active.p;
+    return d;
+}
+
+// Buffers, tables and the operator A of the dense mode (A once per ordinate set).
+int prepare_dense(rom_ctx *ctx)
+{
+    const long long cells = (long long)ctx->J * ctx->NXP;
+    int rc;
+    if ((rc = ensure(ctx, ctx->psi, (size_t)ctx->Mtot * cells * sizeof(float))) ||
+        (rc = ensure(ctx, ctx->src_ord, (size_t)ctx->Mtot * cells * sizeof(float))))
+        return rc;
+    if (!ctx->pmat_dirty) return ROM_OK;
+    std::vector<long long> a_off(ctx->S);
+    long long asz = 0;
+    for (int s = 0; s < ctx->S; ++s) {
+        a_off[s] = asz;
+        asz += (long long)ctx->M[s] * ctx->M[s];
+    }
+    const size_t tb = (size_t)ctx->S * 20;
+    if ((rc = ensure(ctx, ctx->Amat, (size_t)asz * sizeof(float))) || (rc = ensure(ctx, ctx->dtab, tb)))
+        return rc;
+    std::vector<unsigned char> h(tb);
+    memcpy(h.data(), ctx->off.data(), ctx->S * 8);
+    memcpy(h.data() + ctx->S * 8, a_off.data(), ctx->S * 8);
+    memcpy(h.data() + ctx->S * 16, ctx->M.data(), ctx->S * 4);
+    CK(cudaMemcpyAsync(ctx->dtab.p, h.data(), tb, cudaMemcpyHostToDevice, ctx->stream));
+    const DenseTab t = dense_tab(ctx);
+    romk::PmatArgs pa{};
+    pa.S = ctx->S;
+    pa.M = t.M;
+    pa.ord_off = t.ord_off;
+    pa.a_off = t.a_off;
+    pa.c = (const double *)ctx->c64.p;
+    pa.s = (const double *)ctx->s64.p;
+    pa.z = (const double *)ctx->z64.p;
+    pa.w = (const double *)ctx->w64.p;
+    pa.kind = ctx->kernel_kind;
+    pa.g = ctx->g;
+    pa.raw = (ctx->kernel_flags & ROM_KERNEL_FLAG_RAW) ? 1 : 0;
+    pa.normalize = (ctx->kernel_flags & ROM_KERNEL_FLAG_NORMALIZE) ? 1 : 0;
+    pa.A = (float *)ctx->Amat.p;
+    CK(romk::launch_pmat(pa, max_m(ctx), ctx->stream));
+    ++ctx->launches;
+    CK(cudaStreamSynchronize(ctx->stream));  // the host table dies with this call
+    ctx->pmat_dirty = false;
+    return ROM_OK;
+}
+
+// One source-iteration sweep: K1 + K2 (+ K4 in dense mode) + K5.
 int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphConditionalHandle h,
                       cudaEvent_t k0 = nullptr, cudaEvent_t k1 = nullptr)
 {
@@ -355,7 +463,7 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     if (k1) CK(cudaEventRecord(k1, st));
     romk::CombineArgs ca{};
     ca.S = ctx->S;
-    ca.MOM = ctx->MOM;
+    ca.MOM = ctx->MOM == 0 ? 1 : ctx->MOM;
     ca.chunks = ctx->chunks;
     ca.cells = (long long)ctx->J * ctx->NXP;
     ca.cells4 = ca.cells / 4;
@@ -369,6 +477,7 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     ca.active = (const int *)ctx->active.p;
     ca.partials = (double *)ctx->partials.p;
     CK(romk::launch_combine(ca, st));
+    if (ctx->MOM == 0) CK(romk::launch_dense_source(dense_args(ctx), max_m(ctx), st));
     romk::FinalizeArgs fa{};
     fa.S = ctx->S;
     fa.chunks = ctx->chunks;
@@ -438,6 +547,7 @@ void rom_default_options(rom_options *opt)
     opt->check_every = 0;
     opt->tile_g = 0;
     opt->time_kernels = 0;
+    opt->dense_source = 0;
 }
 
 int rom_create(rom_ctx **out, int cuda_device)
@@ -479,7 +589,8 @@ void rom_destroy(rom_ctx *ctx)
                       &ctx->z64, &ctx->w64, &ctx->c32, &ctx->s32, &ctx->w32, &ctx->items_dev,
                       &ctx->item_begin_dev, &ctx->phi, &ctx->src, &ctx->part, &ctx->partials,
                       &ctx->active, &ctx->iters, &ctx->flags, &ctx->resid, &ctx->n_active,
-                      &ctx->avg, &ctx->sum, &ctx->tmp};
+                      &ctx->avg, &ctx->sum, &ctx->tmp, &ctx->psi, &ctx->src_ord, &ctx->Amat,
+                      &ctx->dtab};
     for (DevBuf *b : bufs) release(*b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -512,7 +623,12 @@ int rom_set_options(rom_ctx *ctx, const rom_options *opt)
         return fail(ctx, ROM_ERR_INVALID_ARG, "time_kernels must be 0 or 1");
     if (opt->tile_g != 0 && opt->tile_g != 1 && opt->tile_g != 2 && opt->tile_g != 4)
         return fail(ctx, ROM_ERR_INVALID_ARG, "tile_g must be 0, 1, 2 or 4");
-    if (opt->tile_g != ctx->opt.tile_g) ctx->items_dirty = true;
+    if (opt->dense_source != 0 && opt->dense_source != 1)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "dense_source must be 0 or 1");
+    if (opt->tile_g != ctx->opt.tile_g || opt->dense_source != ctx->opt.dense_source) {
+        ctx->items_dirty = true;
+        ctx->pmat_dirty = true;
+    }
     ctx->opt = *opt;
     invalidate_graph(ctx);
     return ROM_OK;
@@ -858,17 +974,11 @@ int rom_set_kernel(rom_ctx *ctx, int kind, double g, int flags)
     if (!(g > -1.0 && g < 1.0)) return fail(ctx, ROM_ERR_INVALID_ARG, "need -1 < g < 1");
     if (flags & ~(ROM_KERNEL_FLAG_NORMALIZE | ROM_KERNEL_FLAG_RAW))
         return fail(ctx, ROM_ERR_INVALID_ARG, "unknown kernel flags");
-    if (kind == ROM_KERNEL_HG)
-        return fail(ctx, ROM_ERR_UNSUPPORTED, "the Henyey-Greenstein kernel is not built");
-    if (kind == ROM_KERNEL_LINEAR && flags != 0)
-        return fail(ctx, ROM_ERR_UNSUPPORTED,
-                    "the linear kernel is built as the mirror-averaged, unnormalised moment form");
-    const int newmom = kind == ROM_KERNEL_ISO ? 1 : 3;
-    if (newmom != ctx->MOM) invalidate_graph(ctx);
     ctx->kernel_kind = kind;
     ctx->g = kind == ROM_KERNEL_ISO ? 0.0 : g;
     ctx->kernel_flags = flags;
-    ctx->MOM = newmom;
+    ctx->pmat_dirty = true;
+    ctx->items_dirty = true;
     ctx->solved = false;
     invalidate_graph(ctx);
     return ROM_OK;
@@ -882,6 +992,12 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     CK(cudaSetDevice(ctx->device));
     int rc;
     const long long cells = (long long)ctx->J * ctx->NXP;
+    const int mode = source_mode(ctx);
+    if (mode != ctx->MOM) {
+        ctx->MOM = mode;
+        ctx->items_dirty = true;
+        invalidate_graph(ctx);
+    }
     if (ctx->items_dirty) {
         if ((rc = build_items(ctx))) return rc;
         invalidate_graph(ctx);
@@ -894,7 +1010,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     const int chunks = (int)std::max<long long>(1, (cells / 8 + 255) / 256);
     if (chunks != ctx->chunks) invalidate_graph(ctx);
     ctx->chunks = chunks;
-    const int MOM = ctx->MOM;
+    const int MOM = ctx->MOM == 0 ? 1 : ctx->MOM;  // moments kept per sample
     const size_t state = (size_t)ctx->S * MOM * cells * sizeof(float);
     const size_t nI = (size_t)ctx->I * ctx->J;
     void *before[] = {ctx->phi.p, ctx->src.p, ctx->part.p, ctx->partials.p, ctx->active.p};
@@ -909,6 +1025,12 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
         (rc = ensure(ctx, ctx->avg, nI * sizeof(double))) ||
         (rc = ensure(ctx, ctx->sum, nI * sizeof(double))))
         return rc;
+    if (ctx->MOM == 0) {
+        void *dense_before[] = {ctx->psi.p, ctx->src_ord.p, ctx->Amat.p, ctx->dtab.p};
+        if ((rc = prepare_dense(ctx))) return rc;
+        void *dense_after[] = {ctx->psi.p, ctx->src_ord.p, ctx->Amat.p, ctx->dtab.p};
+        if (memcmp(dense_before, dense_after, sizeof dense_before) != 0) invalidate_graph(ctx);
+    }
     void *after[] = {ctx->phi.p, ctx->src.p, ctx->part.p, ctx->partials.p, ctx->active.p};
     if (memcmp(before, after, sizeof before) != 0) invalidate_graph(ctx);
 
@@ -918,6 +1040,11 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
                                (float *)ctx->src.p, (int *)ctx->active.p, (int *)ctx->iters.p,
                                (int *)ctx->flags.p, (double *)ctx->resid.p, ctx->stream));
     ++ctx->launches;
+    if (ctx->MOM == 0) {  // psi^0 = 0: every ordinate's first source is q
+        CK(romk::launch_dense_init((const float *)ctx->q.p, cells, ctx->Mtot,
+                                   (float *)ctx->src_ord.p, ctx->stream));
+        ++ctx->launches;
+    }
     const int cap = ctx->opt.fixed_iters > 0 ? ctx->opt.fixed_iters : ctx->opt.max_iter;
     const bool timed = ctx->opt.time_kernels == 1;
     double sweep_ms = 0.0;
@@ -942,7 +1069,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
                 cudaEvent_t k0 = timed ? ctx->kev[2 * k] : nullptr;
                 cudaEvent_t k1 = timed ? ctx->kev[2 * k + 1] : nullptr;
                 if ((rc = enqueue_iteration(ctx, ctx->stream, false, 0, k0, k1))) return rc;
-                ctx->launches += 3;
+                ctx->launches += ctx->MOM == 0 ? 4 : 3;
             }
             done += n;
             int n_active = 0;
@@ -995,7 +1122,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     st.gpu_ms = ms;
     st.sweep_ms = sweep_ms;
     st.sweep_launches = sweep_launches;
-    if (device_loop) ctx->launches += 3LL * st.iterations_max;
+    if (device_loop) ctx->launches += (ctx->MOM == 0 ? 4LL : 3LL) * st.iterations_max;
     st.kernel_launches = ctx->launches - launches0;
     if (stats_out) *stats_out = st;
     if (diverged) return fail(ctx, ROM_ERR_DIVERGED, "%d samples diverged (NaN/Inf residual)", diverged);
@@ -1015,7 +1142,8 @@ int rom_get_scalar_flux(rom_ctx *ctx, int sample, double *out)
     if (sample >= 0) {
         int rc = ensure(ctx, ctx->tmp, nI * sizeof(double));
         if (rc) return rc;
-        CK(romk::launch_extract((const float *)ctx->phi.p, sample, ctx->MOM, ctx->I, ctx->J,
+        CK(romk::launch_extract((const float *)ctx->phi.p, sample, ctx->MOM == 0 ? 1 : ctx->MOM,
+                                ctx->I, ctx->J,
                                 ctx->NXP, (double *)ctx->tmp.p, ctx->stream));
         ++ctx->launches;
         CK(cudaMemcpyAsync(out, ctx->tmp.p, nI * sizeof(double), cudaMemcpyDeviceToHost,
@@ -1036,7 +1164,8 @@ int rom_get_scalar_flux_device(rom_ctx *ctx, int sample, double *out)
     CK(cudaSetDevice(ctx->device));
     const size_t nI = (size_t)ctx->I * ctx->J;
     if (sample >= 0) {
-        CK(romk::launch_extract((const float *)ctx->phi.p, sample, ctx->MOM, ctx->I, ctx->J,
+        CK(romk::launch_extract((const float *)ctx->phi.p, sample, ctx->MOM == 0 ? 1 : ctx->MOM,
+                                ctx->I, ctx->J,
                                 ctx->NXP, out, ctx->stream));
         ++ctx->launches;
     } else {

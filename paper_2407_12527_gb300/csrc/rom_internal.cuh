@@ -35,8 +35,9 @@ struct SweepArgs {
     float inv_dx, inv_dy;
     float sigma_t_homog;        // used when the grid has one sigma_T
     const float *sigma_t;       // [J][NXP]
-    const float *src;           // [S][MOM][J][NXP]
-    float *part;                // [items][MOM][J][NXP]
+    const float *src;           // [S][MOM][J][NXP]; dense mode: [M_total][J][NXP] per ordinate
+    float *part;                // [items][MOM][J][NXP] (dense mode: one moment, phi)
+    float *psi;                 // dense mode: psi of every ordinate [M_total][J][NXP]
     const SweepItem *items;
     const float *oc, *os, *ow;  // ordinate c, s, w
     const float *inflow;        // nullptr = vacuum; else face values [x_L:J][x_R:J][y_B:I][y_T:I]
@@ -84,6 +85,37 @@ struct OrdGenArgs {
     float *c32, *s32, *w32;
 };
 
+// Dense scattering operator A[l][l'] = w_l' P(u_l', u_l) per sample (K3).
+struct PmatArgs {
+    int S;
+    const int *M;               // [S] ordinates per sample
+    const long long *ord_off;   // [S] first ordinate of the sample
+    const long long *a_off;     // [S] first element of the sample's A (row-major M x M)
+    const double *c, *s, *z, *w;
+    int kind;                   // 0 isotropic, 1 linear, 2 Henyey-Greenstein
+    double g;
+    int raw, normalize;
+    float *A;
+};
+
+// Dense source S_l = sigma_S sum_l' A[l][l'] psi_l' + q for every sample (K4).
+struct DenseArgs {
+    int S;
+    const int *M;
+    const long long *ord_off, *a_off;
+    const float *A;
+    const float *psi;           // [M_total][cells]
+    float *src;                 // [M_total][cells]
+    const float *sigma_s, *q;   // [cells]
+    long long cells;
+    const int *active;
+};
+
+cudaError_t launch_pmat(const PmatArgs &a, int max_m, cudaStream_t st);
+cudaError_t launch_dense_source(const DenseArgs &a, int max_m, cudaStream_t st);
+cudaError_t launch_dense_init(const float *q, long long cells, long long m_total, float *src,
+                              cudaStream_t st);
+
 // 256-bit (one full 32-byte sector) vector accesses of sm_100+, 32-byte aligned.
 __device__ __forceinline__ void ldg8(const float *p, float (&v)[8])
 {
@@ -114,6 +146,8 @@ __device__ __forceinline__ void stg8(float *p, const float (&v)[8])
                  "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]));
 }
 
+// mom: 1 isotropic, 3 linear-kernel moments, 0 dense kernel (per-ordinate
+// source in, psi out).
 cudaError_t launch_sweep2d(const SweepArgs &a, int n_items, int nwarps, int G, int scheme,
                            bool homog, int mom, cudaStream_t st);
 cudaError_t launch_combine(const CombineArgs &a, cudaStream_t st);

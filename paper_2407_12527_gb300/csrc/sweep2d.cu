@@ -101,10 +101,16 @@ struct OrdPacks {
     int ord[G];
 };
 
-// Arrays read per cell: MOM source moments, plus sigma_T when it varies.
-template <int MOM, bool HOMOG>
+// Source modes (template parameter MOM): 1 isotropic (one source moment in,
+// phi out), 3 linear kernel (three source moments in, phi, Jx, Jy out), 0 dense
+// kernel (one source per ordinate in, psi of every ordinate and phi out).
+__host__ __device__ constexpr int n_src(int mom, int g) { return mom == 0 ? g : mom; }
+__host__ __device__ constexpr int n_out(int mom) { return mom == 0 ? 1 : mom; }
+
+// Arrays read per cell: NS sources, plus sigma_T when it varies.
+template <int NS, bool HOMOG>
 struct RowBuf {
-    static constexpr int NA = MOM + (HOMOG ? 0 : 1);
+    static constexpr int NA = NS + (HOMOG ? 0 : 1);
     float v[NA][kH][kCols];
 };
 
@@ -120,9 +126,9 @@ struct RowAddr {
 };
 
 // Issue the loads of the rows of block `blk` (rows past J are skipped).
-template <int MOM, bool HOMOG>
+template <int NS, bool HOMOG>
 __device__ __forceinline__ void load_block(const SweepArgs &A, int blk, bool yneg, int col0,
-                                           const float *__restrict__ src_s, RowBuf<MOM, HOMOG> &b)
+                                           const float *const (&srcp)[NS], RowBuf<NS, HOMOG> &b)
 {
     const RowAddr ra(A, blk, yneg, col0);
 #pragma unroll
@@ -130,13 +136,24 @@ __device__ __forceinline__ void load_block(const SweepArgs &A, int blk, bool yne
         if (blk * kH + h < A.J) {
             const long long row = ra.base + h * ra.rs;
 #pragma unroll
-            for (int m = 0; m < MOM; ++m) ld8(src_s + m * A.cells + row, b.v[m][h]);
-            if (!HOMOG) ld8(A.sigma_t + row, b.v[MOM][h]);
+            for (int m = 0; m < NS; ++m) ld8(srcp[m] + row, b.v[m][h]);
+            if (!HOMOG) ld8(A.sigma_t + row, b.v[NS][h]);
         }
     }
 }
 
 // One H x 8 block of cells for all G ordinates of the item, from the rows in b.
+// Cell value psi_c of the ordinates of pack p at column r, kept for the row store.
+__device__ __forceinline__ void psi_put(float (&row)[1][kCols], int, int r, float v) { row[0][r] = v; }
+template <int R>
+__device__ __forceinline__ void psi_put(float (&row)[R][kCols], int p, int r, float2 v)
+{
+    if constexpr (R >= 2) {
+        row[(2 * p) % R][r] = v.x;
+        row[(2 * p + 1) % R][r] = v.y;
+    }
+}
+
 // The block's moments are left in out[][][] (LATE: the caller stores them
 // after the shuffle), or stored row by row at part_i (three moments: the
 // registers for holding them are not there).
@@ -146,10 +163,11 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &A, int blk, bool yn
                                             typename Pack<G>::T (&py)[kCols][Pack<G>::N],
                                             const typename Pack<G>::T (&xin)[kH][Pack<G>::N],
                                             typename Pack<G>::T (&xo)[kH][Pack<G>::N],
-                                            const RowBuf<MOM, HOMOG> &b,
-                                            float (&out)[LATE ? MOM : 1][kH][kCols],
+                                            const RowBuf<n_src(MOM, G), HOMOG> &b,
+                                            float (&out)[LATE ? n_out(MOM) : 1][kH][kCols],
                                             float *__restrict__ part_i)
 {
+    constexpr int NS = n_src(MOM, G);
     using T = typename Pack<G>::T;
     constexpr int N = Pack<G>::N;
     const T two = splat<T>(2.f);
@@ -166,6 +184,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &A, int blk, bool yn
         T acc0[kCols], acc1[kCols], acc2[kCols];
 #pragma unroll
         for (int r = 0; r < kCols; ++r) acc0[r] = acc1[r] = acc2[r] = splat<T>(0.f);
+        float psi_row[MOM == 0 ? G : 1][kCols];  // dense mode: psi of the row, per ordinate
 #pragma unroll
         for (int rr = 0; rr < kCols; ++rr) {
             const int r = XNEG ? (kCols - 1 - rr) : rr;
@@ -176,10 +195,18 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &A, int blk, bool yn
                 T S = s0;
                 if (MOM == 3)
                     S = fma_(o.c[p], splat<T>(b.v[1][h][r]), fma_(o.s[p], splat<T>(b.v[2][h][r]), S));
+                if (MOM == 0) {  // per-ordinate sources of the pack
+                    if constexpr (G == 1) setc(S, 0, b.v[0][h][r]);
+                    else {
+                        setc(S, 0, b.v[(2 * p) % NS][h][r]);
+                        setc(S, 1, b.v[(2 * p + 1) % NS][h][r]);
+                    }
+                }
                 if (HOMOG && SCHEME == 0) {
                     const T s2 = mul_(S, o.r2[p]);                 // 2 rd S
                     const T xn = fma_(o.al[p], x[p], fma_(o.b2[p], py[r][p], s2));
                     const T pyn = fma_(o.a2[p], x[p], fma_(o.be[p], py[r][p], s2));
+                    if (MOM == 0) psi_put(psi_row, p, r, mul_(add_(x[p], xn), splat<T>(0.5f)));
                     if (ok) {
                         acc0[r] = fma_(o.wh[p], add_(x[p], xn), acc0[r]);
                         if (MOM == 3) {
@@ -192,6 +219,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &A, int blk, bool yn
                     }
                 } else if (HOMOG) {
                     const T pc = fma_(o.ar[p], x[p], fma_(o.br[p], py[r][p], mul_(S, o.rd[p])));
+                    if (MOM == 0) psi_put(psi_row, p, r, pc);
                     if (ok) {
                         x[p] = pc;
                         py[r][p] = pc;
@@ -204,8 +232,9 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &A, int blk, bool yn
                 } else {
                     const T num = fma_(o.a[p], x[p], fma_(o.b[p], py[r][p], S));
                     const T rden =
-                        rcp_(add_(splat<T>(b.v[RowBuf<MOM, HOMOG>::NA - 1][h][r]), o.ab[p]));
+                        rcp_(add_(splat<T>(b.v[RowBuf<NS, HOMOG>::NA - 1][h][r]), o.ab[p]));
                     const T pc = mul_(num, rden);
+                    if (MOM == 0) psi_put(psi_row, p, r, pc);
                     if (ok) {
                         if (SCHEME == 0) {
                             x[p] = fma_(two, pc, neg_(x[p]));
@@ -241,6 +270,11 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &A, int blk, bool yn
 #pragma unroll
             for (int r = 0; r < kCols; ++r) v[r] = hsum(acc0[r]);
             st8(part_i + ra.base + h * ra.rs, v);
+            if constexpr (MOM == 0) {
+#pragma unroll
+                for (int k = 0; k < G; ++k)
+                    st8(A.psi + (long long)o.ord[k] * A.cells + ra.base + h * ra.rs, psi_row[k]);
+            }
             if (MOM == 3) {
 #pragma unroll
                 for (int r = 0; r < kCols; ++r) v[r] = hsum(acc1[r]);
@@ -290,30 +324,36 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
 #pragma unroll
         for (int p = 0; p < N; ++p) xin[h][p] = splat<T>(0.f);
 
-    const float *src_s = A.src + (long long)it.sample * MOM * A.cells;
-    float *part_i = A.part + (long long)blockIdx.x * MOM * A.cells;
+    constexpr int NS = n_src(MOM, G);
+    // source arrays of the item: the sample's moments, or (dense) one per ordinate
+    const float *srcp[NS];
+#pragma unroll
+    for (int m = 0; m < NS; ++m)
+        srcp[m] = MOM == 0 ? A.src + (long long)o.ord[m] * A.cells
+                           : A.src + ((long long)it.sample * MOM + m) * A.cells;
+    float *part_i = A.part + (long long)blockIdx.x * n_out(MOM) * A.cells;
 
     // The rows of the lane's block for step t + PD are loaded at the start of
     // step t into a ring of PD + 1 register buffers indexed by t (the same index
     // for every lane: lane d at step t works on block t - d).  With more than
     // two arrays per cell (linear kernel) the registers are not there; the rows
     // are then loaded at the start of their step.
-    constexpr int NA = RowBuf<MOM, HOMOG>::NA;
+    constexpr int NA = RowBuf<NS, HOMOG>::NA;
     constexpr bool PF = NA <= 2;
     constexpr int PD = NA == 1 ? kPrefetch : (NA == 2 ? 1 : 0);
     // moments are stored row by row inside the block (holding a whole block's
     // moments until the end of the step measured slower on GB300)
     constexpr bool STORE_LATE = false;
-    RowBuf<MOM, HOMOG> buf[PD + 1];
-    auto step = [&](int t, RowBuf<MOM, HOMOG> &cur, RowBuf<MOM, HOMOG> &nxt) {
+    RowBuf<NS, HOMOG> buf[PD + 1];
+    auto step = [&](int t, RowBuf<NS, HOMOG> &cur, RowBuf<NS, HOMOG> &nxt) {
         const int blk = t - d;
         const bool active = lane_on && blk >= 0 && blk < nblk;
         if (PF && lane_on && blk + PD >= 0 && blk + PD < nblk)
-            load_block<MOM, HOMOG>(A, blk + PD, yneg, col0, src_s, nxt);
+            load_block<NS, HOMOG>(A, blk + PD, yneg, col0, srcp, nxt);
         T xo[kH][N];
-        float out[STORE_LATE ? MOM : 1][kH][kCols];
+        float out[STORE_LATE ? n_out(MOM) : 1][kH][kCols];
         if (active) {
-            if (!PF) load_block<MOM, HOMOG>(A, blk, yneg, col0, src_s, cur);
+            if (!PF) load_block<NS, HOMOG>(A, blk, yneg, col0, srcp, cur);
             if (d == 0) {  // incoming x-edge values (face x_L, or x_R when c < 0)
 #pragma unroll
                 for (int h = 0; h < kH; ++h)
@@ -354,7 +394,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
             for (int h = 0; h < kH; ++h)
                 if (blk * kH + h < A.J)
 #pragma unroll
-                    for (int m = 0; m < (STORE_LATE ? MOM : 1); ++m)
+                    for (int m = 0; m < (STORE_LATE ? n_out(MOM) : 1); ++m)
                         st8(part_i + m * A.cells + ra.base + h * ra.rs, out[m][h]);
         }
         if (nwarps > 1) {
@@ -382,7 +422,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
 #pragma unroll
         for (int k = 0; k < PD; ++k)
             if (lane_on && k - d >= 0 && k - d < nblk)
-                load_block<MOM, HOMOG>(A, k - d, yneg, col0, src_s, buf[k]);
+                load_block<NS, HOMOG>(A, k - d, yneg, col0, srcp, buf[k]);
         int t = 0;
         for (; t + PD < T_steps; t += PD + 1) {
 #pragma unroll
@@ -471,6 +511,10 @@ cudaError_t launch_sweep2d(const SweepArgs &a, int n_items, int nwarps, int G, i
         if (G == 1) return launch_g<1, 3>(a, n_items, nwarps, scheme, homog, st);
         if (G == 2) return launch_g<2, 3>(a, n_items, nwarps, scheme, homog, st);
         if (G == 4) return launch_g<4, 3>(a, n_items, nwarps, scheme, homog, st);
+    } else if (mom == 0) {
+        if (G == 1) return launch_g<1, 0>(a, n_items, nwarps, scheme, homog, st);
+        if (G == 2) return launch_g<2, 0>(a, n_items, nwarps, scheme, homog, st);
+        if (G == 4) return launch_g<4, 0>(a, n_items, nwarps, scheme, homog, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -35,15 +35,15 @@ def rel(a, b):
 
 
 def gpu_solve(R, I, J, bounds, st, ss, q, sets=None, seed=None, nz=None, nt=None, kernel="iso",
-              g=0.0, inflow=None, inflow_ord=None, **opts):
+              g=0.0, inflow=None, inflow_ord=None, flags=0, **opts):
     ctx = R.RomContext(0)
     ctx.set_grid(I, J, bounds, st, ss, q)
     if sets is not None:
         ctx.set_ordinates([(o.c, o.s, o.zeta, o.w) for o in sets])
     else:
         ctx.set_ordinates_seed(seed, nz, nt)
-    if kernel != "iso":
-        ctx.set_kernel(kernel, g)
+    if kernel != "iso" or flags:
+        ctx.set_kernel(kernel, g, flags)
     if inflow is not None:
         off = [0, J, 2 * J, 2 * J + I, 2 * J + 2 * I]
         for f in range(4):
@@ -268,8 +268,11 @@ def test_invalid_arguments_rejected(rom):
     with pytest.raises(rom.RomError):
         ctx.set_ordinates([(np.array([0.9]), np.array([0.9]), np.array([0.1]), np.array([1.0]))])
     with pytest.raises(rom.RomError) as e:
-        ctx.set_kernel("hg", 0.8)
-    assert e.value.code == -7
+        ctx.set_kernel("hg", 1.0)
+    assert e.value.code == -1
+    with pytest.raises(rom.RomError) as e:
+        ctx.set_grid(4, 4, (0, 1, 0, 1), 1.0, 0.5, 1.0) or ctx.set_options(dense_source=2)
+    assert e.value.code == -1
     ctx.close()
 
 
@@ -305,3 +308,50 @@ def test_point_source_full_size_sampled(rom):
         assert rel(gpu["phi"][k], ref["phi"][0]) < TOL, k
     assert np.all(gpu["resid"] < 1e-6)
     np.testing.assert_allclose(gpu["avg"], gpu["phi"].astype(np.float64).mean(0), rtol=1e-12)
+
+
+# ------------------------------------------------ dense scattering operator
+
+@pytest.mark.parametrize("flags", [0, 1, 2])
+def test_hg_dense_parity(rom, flags):
+    """Henyey-Greenstein kernel through the dense operator A = w_l' P(u_l', u_l)
+    (eq. wl): uneven M per sample (20, 16, 48 -- partial GEMM tiles, M not a
+    multiple of 8), heterogeneous medium; flags 1 = row-normalised (Remark,
+    Sec. 3.1), 2 = raw hemisphere kernel."""
+    I, J = 53, 41
+    bounds = (0.0, 1.0, 0.0, 0.8)
+    st, ss, q = W.random_medium(I, J, seed=71, ratio_max=0.8)
+    nz, nt = [1, 2, 2], [5, 2, 6]
+    gpu = gpu_solve(rom, I, J, bounds, st, ss, q, seed=73, nz=nz, nt=nt, kernel="hg", g=0.8,
+                    fixed_iters=5, flags=flags)
+    sets = [O.rom_ordinates_xy(73, k, nz[k], nt[k]) for k in range(3)]
+    ref = O.solve_xy(I, J, bounds, st, ss, q, sets, kernel="hg", g=0.8, fixed_iters=5,
+                     normalize_rows=bool(flags & 1), raw=bool(flags & 2))
+    for k in range(3):
+        assert rel(gpu["phi"][k], ref["phi"][k]) < TOL, k
+
+
+def test_hg_dense_full_tiles(rom):
+    """M = 128 random ordinates per sample (full 128 x 128 operator tiles), uniform
+    medium, the 512 x 512 disc problem shrunk to 96 x 96."""
+    p = W.hg_disc(n=96, n_samples=2)
+    nz, nt = [4, 4], [8, 8]
+    gpu = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, seed=W.ordinate_seed(3),
+                    nz=nz, nt=nt, kernel="hg", g=0.8, fixed_iters=4)
+    sets = [O.rom_ordinates_xy(W.ordinate_seed(3), k, 4, 8) for k in range(2)]
+    ref = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, sets, kernel="hg", g=0.8,
+                     fixed_iters=4)
+    for k in range(2):
+        assert rel(gpu["phi"][k], ref["phi"][k]) < TOL, k
+
+
+@pytest.mark.parametrize("kernel,g", [("iso", 0.0), ("linear", 0.9)])
+def test_dense_operator_equals_moment_path(rom, kernel, g):
+    p = W.example_2_1(I=40, J=36, g=g)
+    nz, nt = [2, 1], [2, 3]
+    a = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, seed=5, nz=nz, nt=nt,
+                  kernel=kernel, g=g, fixed_iters=6)
+    b = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, seed=5, nz=nz, nt=nt,
+                  kernel=kernel, g=g, fixed_iters=6, dense_source=1)
+    for k in range(2):
+        assert rel(b["phi"][k], a["phi"][k]) < TOL
