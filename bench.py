@@ -37,17 +37,73 @@ import rom_workloads as W  # noqa: E402
 METRIC = "cell-ordinate updates/s (ROM source iteration, 1 GB300)"
 UNIT = "updates/s"
 FLOP_PER_UPDATE = 11  # diamond difference, homogeneous sigma_T: 5 FMA + 1 MUL
-N_SAMPLES, NZ, NT, TOL = 64, 2, 2, 1e-6
-SEED = W.ordinate_seed(1)
+FLOP_PER_UPDATE_HET = 13  # heterogeneous sigma_T: + 1 add + 1 reciprocal per cell-ordinate
+TOL = 1e-6
+
+
+class Workload:
+    """One benchmark workload: a problem of rom_workloads, its ordinate sets per
+    step (seeded ROM partitions, or one deterministic DOM set) and kernel."""
+
+    def __init__(self, name, problem, desc, nz=None, nt=None, quad=None, kernel="iso", g=0.0,
+                 cfg_index=1):
+        self.name, self.p, self.desc = name, problem, desc
+        self.nz, self.nt, self.quad = nz, nt, quad
+        self.kernel, self.g = kernel, g
+        self.seed = W.ordinate_seed(cfg_index)
+
+    @property
+    def samples(self):
+        return 1 if self.quad else len(self.nz)
+
+    def m_total(self):
+        if self.quad:
+            from paper_2407_12527_gb300 import quadrature_xy
+            return quadrature_xy(*self.quad)[0].shape[0]
+        return int(sum(4 * a * b for a, b in zip(self.nz, self.nt)))
+
+
+def make_workload(name):
+    partition = W.partition
+    if name == "point_source":
+        p = W.point_source()
+        return Workload(name, p, "point_source_256 (256x256 on [-1,1]^2, sigma_T=1, sigma_S=0.9 "
+                        "isotropic, Gaussian q std 0.02, vacuum): ROM 64 samples x 16 ordinates, "
+                        "SI to 1e-6", nz=[2] * 64, nt=[2] * 64, cfg_index=1)
+    if name == "point_source_dom":
+        p = W.point_source()
+        return Workload(name, p, "point_source_256, plain DOM with the 2D uniform set N = 8 "
+                        "(256 ordinates), SI to 1e-6", quad=("uniform", 8, 0), cfg_index=1)
+    if name == "dom_small":
+        p = W.dom_small()
+        return Workload(name, p, "dom_small_32x32 (sigma_T=1, sigma_S=0.5, central 8x8 source), "
+                        "DOM product set 4 Gauss-Legendre polar x 8 azimuthal = 32, SI to 1e-6",
+                        quad=("product_gl", 4, 8), cfg_index=0)
+    if name == "checkerboard":
+        p = W.checkerboard()
+        parts = [partition(m) for m in p.ordinates["m_quadrant"]]
+        return Workload(name, p, "checkerboard_448 (7x7 blocks of 64x64; absorber sigma_T=10, "
+                        "background sigma_T=1, sigma_S=0.9; centre q=1): 256 ROM samples, M "
+                        "uniform in {8,16,32,64}, one launch per sweep, SI to 1e-6",
+                        nz=[a for a, _ in parts], nt=[b for _, b in parts], cfg_index=2)
+    if name == "hg_disc":
+        p = W.hg_disc()
+        return Workload(name, p, "hg_disc_512 (512x512, sigma_T=1, sigma_S=0.95, Henyey-Greenstein "
+                        "g=0.8, q=1 in a disc r<=0.05): ROM 32 samples x 128 ordinates, dense "
+                        "operator (FP32 GEMM), SI to 1e-6", nz=[4] * 32, nt=[8] * 32,
+                        kernel="hg", g=0.8, cfg_index=3)
+    raise SystemExit(f"unknown workload {name}")
+
+
+WL = None  # the workload of this run (set in main)
 
 
 def workload_config(extra=None):
-    p = W.point_source()
+    p = WL.p
     cfg = {
-        "workload": "point_source_256 (256x256 on [-1,1]^2, sigma_T=1, sigma_S=0.9 isotropic, "
-                    "Gaussian q std 0.02, vacuum): ROM 64 samples x 16 ordinates, SI to 1e-6",
-        "grid": [p.I, p.J], "samples_per_step": N_SAMPLES, "ordinates_per_sample": 4 * NZ * NT,
-        "si_tol": TOL, "scheme": "diamond difference", "kernel": "isotropic",
+        "workload": WL.desc, "grid": [p.I, p.J], "samples_per_step": WL.samples,
+        "ordinates_per_step": WL.m_total(), "si_tol": TOL, "scheme": "diamond difference",
+        "kernel": WL.kernel + (f" g={WL.g}" if WL.g else ""),
         "l2": "flushed between steps (256 MiB write outside the timed events)",
     }
     if extra:
@@ -148,24 +204,42 @@ def barrier(world):
 
 # ------------------------------------------------------------ CPU oracle
 
+def oracle_sets(first: int, count: int):
+    """The oracle's ordinate sets for samples first .. first+count-1 of the workload
+    (its own generator and quadratures)."""
+    from oracle import oracle as O
+    if WL.quad:
+        kind, n1, n2 = WL.quad
+        maker = {"uniform": lambda: O.quad_uniform_xy(n1), "gauss": lambda: O.quad_gauss_xy(n1),
+                 "product_gl": lambda: O.quad_product_gl_xy(n1, n2)}[kind]
+        return [maker()]
+    S = WL.samples
+    return [O.rom_ordinates_xy(WL.seed, first + k, WL.nz[(first + k) % S], WL.nt[(first + k) % S])
+            for k in range(count)]
+
+
 def oracle_rate(budget_s: float, max_samples: int, first: int = 0):
     """The FP64 oracle, as it stands, on consecutive samples of the workload until
-    the time budget is used: returns (updates/s, samples, threads, updates)."""
+    the time budget is used (the dense kernel: one source-iteration sweep per
+    sample, its cost being M^2 per cell): returns (updates/s, samples, threads,
+    updates, seconds)."""
     from oracle import oracle as O
-    p = W.point_source()
+    p = WL.p
     threads = O.max_threads()
-    upd = 0
-    n = 0
+    upd, n, m_max = 0, 0, 1
     t0 = time.perf_counter()
     while n < max_samples:
-        o = O.rom_ordinates_xy(SEED, first + n, NZ, NT)
-        r = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, [o], tol=TOL)
+        o = oracle_sets(first + n, 1)[0]
+        kw = {"fixed_iters": 1} if WL.kernel == "hg" else {"tol": TOL}
+        r = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, [o], kernel=WL.kernel,
+                       g=WL.g, allow_not_converged=True, **kw)
         upd += p.I * p.J * o.M * int(r["iters"][0])
+        m_max = max(m_max, o.M)
         n += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return upd / dt, n, min(threads, 4 * NZ * NT), upd, dt
+    return upd / dt, n, min(threads, m_max), upd, dt
 
 
 def run_reference(args):
@@ -179,7 +253,8 @@ def run_reference(args):
     t_tot, upd_tot, ns_tot = 0.0, 0, 0
     threads = 1
     for k in range(args.steps):
-        rate, ns, threads, upd, dt = oracle_rate(per_step, 64, first=N_SAMPLES * (k + 1))
+        rate, ns, threads, upd, dt = oracle_rate(per_step, WL.samples,
+                                                 first=WL.samples * (k + 1))
         t_tot += dt
         upd_tot += upd
         ns_tot += ns
@@ -191,7 +266,7 @@ def run_reference(args):
         "data": "synthetic",
         "config": workload_config({"reference": "FP64 CPU oracle (oracle/rom_oracle.c, OpenMP)"}),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{ns_tot} ROM samples of the workload over {args.steps} "
+                         "sample": f"{ns_tot} ordinate sets of the workload over {args.steps} "
                                    f"steps (each step about {per_step:.2f} s of CPU work)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -214,11 +289,14 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_2407_12527_gb300 import RomContext
 
-    p = W.point_source()
-    nz = [NZ] * N_SAMPLES
-    nt = [NT] * N_SAMPLES
+    p = WL.p
+    S = WL.samples
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def setup(ctx):
+        if WL.kernel != "iso":
+            ctx.set_kernel(WL.kernel, WL.g)
 
     ctx = RomContext(local)
     ctx.set_stream(stream.cuda_stream)
@@ -226,14 +304,23 @@ def run_ours(args):
                        for a in (p.sigma_t, p.sigma_s, p.q))
     torch.cuda.synchronize(dev)
     ctx.set_grid_device(p.I, p.J, p.bounds, st_d, ss_d, q_d)
+    setup(ctx)
     ctx.set_options(tol=TOL, check_every=args.check_every, tile_g=args.tile_g)
 
     def first_sample(step):
-        return (step * world + rank) * N_SAMPLES
+        return (step * world + rank) * S
+
+    def set_ordinates(c, step):
+        if WL.quad:
+            if step == 0 or getattr(c, "_quad_set", False) is False:
+                c.set_quadrature(*WL.quad)
+                c._quad_set = True
+        else:
+            c.set_ordinates_seed(WL.seed, WL.nz, WL.nt, first_sample=first_sample(step))
 
     def one_step(step):
-        ctx.set_ordinates_seed(SEED, nz, nt, first_sample=first_sample(step))
-        return ctx.solve()
+        set_ordinates(ctx, step)
+        return ctx.solve(allow_not_converged=True)
 
     for k in range(args.warmup):
         one_step(10_000 + k)
@@ -255,7 +342,7 @@ def run_ours(args):
         stream.synchronize()
         ms.append(e0.elapsed_time(e1))
         upd += s["updates"]
-        launches += 1 + s["kernel_launches"]  # ordinate generation + the solve's kernels
+        launches += (0 if WL.quad else 1) + s["kernel_launches"]  # ordinate generation + solve
         iters.append(s["iterations_max"])
     torch.cuda.synchronize(dev)
     barrier(world)
@@ -269,13 +356,16 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                               "steps": args.steps, "warmup": args.warmup,
-                              "ms_per_step": 1e3 * t_max / args.steps, "only_timed": True}))
+                              "ms_per_step": 1e3 * t_max / args.steps, "only_timed": True,
+                              "workload": WL.name}))
         ctx.close()
         return 0
 
-    # roofline: the same steps with CUDA events around every sweep launch
+    # roofline: the same steps with CUDA events around every sweep (and, for the dense
+    # operator, every contraction) launch
     ctx.set_options(tol=TOL, time_kernels=1, check_every=8, tile_g=args.tile_g)
-    sweep_ms, sweep_upd, sweep_n = 0.0, 0, 0
+    sweep_ms, sweep_upd, sweep_n, src_ms, src_n = 0.0, 0, 0, 0.0, 0
+    src_flop = 0.0
     for k in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -283,15 +373,30 @@ def run_ours(args):
         sweep_ms += s["sweep_ms"]
         sweep_upd += s["updates"]
         sweep_n += s["sweep_launches"]
-    ctx.set_options(tol=TOL, tile_g=args.tile_g)
+        src_ms += s["source_ms"]
+        src_n += s["source_launches"]
+        if WL.kernel == "hg":  # 2 M^2 flops per cell and contraction, per active sample
+            it, _ = ctx.iterations()
+            M = 4 * WL.nz[0] * WL.nt[0]
+            src_flop += 2.0 * M * M * p.I * p.J * float(np.sum(it))
+    ctx.set_options(tol=TOL, check_every=args.check_every, tile_g=args.tile_g)
     peak_tflops = 152 * 128 * 2 * 2070e6 / 1e12
-    achieved = sweep_upd * FLOP_PER_UPDATE / (sweep_ms / 1e3) / 1e12
+    homog = float(np.min(p.sigma_t)) == float(np.max(p.sigma_t))
+    fpu = FLOP_PER_UPDATE if homog else FLOP_PER_UPDATE_HET
+    if WL.kernel == "hg" and src_ms > 0:
+        achieved = src_flop / (src_ms / 1e3) / 1e12
+        kernel_name, n_l, avg_us, fu = ("dense_source_kernel (K4, FP32 SIMT GEMM)", src_n,
+                                        1e3 * src_ms / max(src_n, 1), None)
+    else:
+        achieved = sweep_upd * fpu / (sweep_ms / 1e3) / 1e12
+        kernel_name, n_l, avg_us, fu = ("sweep2d_kernel (K1)", sweep_n,
+                                        1e3 * sweep_ms / max(sweep_n, 1), fpu)
     # DRAM bytes of one full sweep launch from the committed ncu capture, used
     # only while the sweep source is the one that was captured
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "sweep2d_point_source_256x64.traffic.json")
     spath = os.path.join(ROOT, "paper_2407_12527_gb300", "csrc", "sweep2d.cu")
-    if os.path.exists(tpath) and args.tile_g in (0, 2):
+    if WL.name == "point_source" and os.path.exists(tpath) and args.tile_g in (0, 2):
         import hashlib
         with open(tpath) as f:
             tr = json.load(f)
@@ -302,13 +407,13 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "traffic_note": "DRAM read+write bytes of one full sweep launch (ncu)",
-                "kernel": "sweep2d_kernel (K1)",
-                "launches": sweep_n, "avg_launch_us": 1e3 * sweep_ms / max(sweep_n, 1),
-                "flop_per_update": FLOP_PER_UPDATE,
+                "kernel": kernel_name, "launches": n_l, "avg_launch_us": avg_us,
+                "flop_per_update": fu, "sweep_avg_launch_us": 1e3 * sweep_ms / max(sweep_n, 1),
                 "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 flop x 2070 MHz"}
 
     # end to end through the C ABI with host buffers
     ctx2 = RomContext(local)
+    setup(ctx2)
     ctx2.set_options(tol=TOL, tile_g=args.tile_g)
     st_h, ss_h, q_h = (np.ascontiguousarray(a, dtype=np.float64) for a in
                        (p.sigma_t, p.sigma_s, p.q))
@@ -317,8 +422,9 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         ctx2.set_grid(p.I, p.J, p.bounds, st_h, ss_h, q_h)
-        ctx2.set_ordinates_seed(SEED, nz, nt, first_sample=first_sample(k))
-        s = ctx2.solve()
+        ctx2._quad_set = False
+        set_ordinates(ctx2, k)
+        s = ctx2.solve(allow_not_converged=True)
         phi_bar = ctx2.scalar_flux(-1)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
@@ -334,10 +440,11 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, ns, threads, _, dt = oracle_rate(args.cpu_budget, N_SAMPLES)
+        rate, ns, threads, _, dt = oracle_rate(args.cpu_budget, S)
+        what = "one source-iteration sweep of each" if WL.kernel == "hg" else "solved to 1e-6"
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {ns} of the 64 ROM samples of one step, solved one after "
-                         f"another to 1e-6 ({dt:.1f} s)"}
+               "sample": f"first {ns} of the {S} ordinate sets of one step, one after another, "
+                         f"{what} ({dt:.1f} s)"}
 
     if rank == 0:
         line = {
@@ -374,7 +481,12 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-total", type=float, default=60.0,
                     help="CPU seconds the reference (oracle) arm spends over all its steps")
+    ap.add_argument("--workload", default="point_source",
+                    choices=["point_source", "point_source_dom", "dom_small", "checkerboard",
+                             "hg_disc"])
     args = ap.parse_args()
+    global WL
+    WL = make_workload(args.workload)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

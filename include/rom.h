@@ -101,6 +101,8 @@ typedef struct rom_stats {
     int64_t kernel_launches; /* kernels the solve launched (graph nodes counted per run) */
     double sweep_ms;         /* summed duration of the sweep kernels (time_kernels = 1)   */
     int64_t sweep_launches;  /* sweep kernels timed                                       */
+    double source_ms;        /* summed duration of the dense-operator contractions        */
+    int64_t source_launches; /* contractions timed (dense operator only)                  */
 } rom_stats;
 
 /* ------------------------------------------------------------- lifetime */

@@ -452,7 +452,8 @@ int prepare_dense(rom_ctx *ctx)
 
 // One source-iteration sweep: K1 + K2 (+ K4 in dense mode) + K5.
 int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphConditionalHandle h,
-                      cudaEvent_t k0 = nullptr, cudaEvent_t k1 = nullptr)
+                      cudaEvent_t k0 = nullptr, cudaEvent_t k1 = nullptr,
+                      cudaEvent_t k2 = nullptr, cudaEvent_t k3 = nullptr)
 {
     const romk::SweepArgs sa = sweep_args(ctx);
     const int L = (ctx->I + romk::kCols - 1) / romk::kCols;
@@ -477,7 +478,11 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     ca.active = (const int *)ctx->active.p;
     ca.partials = (double *)ctx->partials.p;
     CK(romk::launch_combine(ca, st));
-    if (ctx->MOM == 0) CK(romk::launch_dense_source(dense_args(ctx), max_m(ctx), st));
+    if (ctx->MOM == 0) {
+        if (k2) CK(cudaEventRecord(k2, st));
+        CK(romk::launch_dense_source(dense_args(ctx), max_m(ctx), st));
+        if (k3) CK(cudaEventRecord(k3, st));
+    }
     romk::FinalizeArgs fa{};
     fa.S = ctx->S;
     fa.chunks = ctx->chunks;
@@ -1047,16 +1052,16 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     }
     const int cap = ctx->opt.fixed_iters > 0 ? ctx->opt.fixed_iters : ctx->opt.max_iter;
     const bool timed = ctx->opt.time_kernels == 1;
-    double sweep_ms = 0.0;
-    long long sweep_launches = 0;
+    double sweep_ms = 0.0, source_ms = 0.0;
+    long long sweep_launches = 0, source_launches = 0;
     const bool device_loop = ctx->opt.check_every == 0 && !timed;
     if (device_loop) {
         if (!ctx->graph_valid && (rc = build_graph(ctx))) return rc;
         CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
     } else {
         const int every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 1;
-        if (timed && ctx->kev.size() < 2 * (size_t)every) {
-            while (ctx->kev.size() < 2 * (size_t)every) {
+        if (timed && ctx->kev.size() < 4 * (size_t)every) {
+            while (ctx->kev.size() < 4 * (size_t)every) {
                 cudaEvent_t e;
                 CK(cudaEventCreate(&e));
                 ctx->kev.push_back(e);
@@ -1066,9 +1071,11 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
         while (done < cap) {
             const int n = std::min(every, cap - done);
             for (int k = 0; k < n; ++k) {
-                cudaEvent_t k0 = timed ? ctx->kev[2 * k] : nullptr;
-                cudaEvent_t k1 = timed ? ctx->kev[2 * k + 1] : nullptr;
-                if ((rc = enqueue_iteration(ctx, ctx->stream, false, 0, k0, k1))) return rc;
+                cudaEvent_t k0 = timed ? ctx->kev[4 * k] : nullptr;
+                cudaEvent_t k1 = timed ? ctx->kev[4 * k + 1] : nullptr;
+                cudaEvent_t k2 = timed && ctx->MOM == 0 ? ctx->kev[4 * k + 2] : nullptr;
+                cudaEvent_t k3 = timed && ctx->MOM == 0 ? ctx->kev[4 * k + 3] : nullptr;
+                if ((rc = enqueue_iteration(ctx, ctx->stream, false, 0, k0, k1, k2, k3))) return rc;
                 ctx->launches += ctx->MOM == 0 ? 4 : 3;
             }
             done += n;
@@ -1079,9 +1086,14 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
             if (timed)
                 for (int k = 0; k < n; ++k) {
                     float ms = 0.f;
-                    CK(cudaEventElapsedTime(&ms, ctx->kev[2 * k], ctx->kev[2 * k + 1]));
+                    CK(cudaEventElapsedTime(&ms, ctx->kev[4 * k], ctx->kev[4 * k + 1]));
                     sweep_ms += ms;
                     ++sweep_launches;
+                    if (ctx->MOM == 0) {
+                        CK(cudaEventElapsedTime(&ms, ctx->kev[4 * k + 2], ctx->kev[4 * k + 3]));
+                        source_ms += ms;
+                        ++source_launches;
+                    }
                 }
             if (n_active == 0) break;
         }
@@ -1122,6 +1134,8 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     st.gpu_ms = ms;
     st.sweep_ms = sweep_ms;
     st.sweep_launches = sweep_launches;
+    st.source_ms = source_ms;
+    st.source_launches = source_launches;
     if (device_loop) ctx->launches += (ctx->MOM == 0 ? 4LL : 3LL) * st.iterations_max;
     st.kernel_launches = ctx->launches - launches0;
     if (stats_out) *stats_out = st;

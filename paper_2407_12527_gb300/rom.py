@@ -41,7 +41,8 @@ class rom_stats(ctypes.Structure):
                 ("iterations_min", ctypes.c_int), ("n_not_converged", ctypes.c_int),
                 ("updates", ctypes.c_int64), ("residual_max", ctypes.c_double),
                 ("gpu_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
-                ("sweep_ms", ctypes.c_double), ("sweep_launches", ctypes.c_int64)]
+                ("sweep_ms", ctypes.c_double), ("sweep_launches", ctypes.c_int64),
+                ("source_ms", ctypes.c_double), ("source_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

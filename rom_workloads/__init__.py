@@ -155,6 +155,13 @@ def random_inflow(I: int, J: int, seed: int, per_ordinate_M: int = 0, scale: flo
     return rng.uniform(0.0, scale, size=n)
 
 
+def partition(m: int):
+    """(n_zeta, n_theta) for m cells per quadrant: n_zeta the largest divisor of m that
+    is <= sqrt(m) (N x N when m = N^2).  A workload parameter, used by both paths."""
+    nz = max(d for d in range(1, int(np.sqrt(m)) + 1) if m % d == 0)
+    return nz, m // nz
+
+
 def ordinate_seed(config_index: int, rep: int = 0) -> int:
     """Seed convention for the ROM draws of a workload: 1000 * config + rep."""
     return 1000 * config_index + rep
