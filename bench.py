@@ -396,7 +396,7 @@ def run_ours(args):
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "sweep2d_point_source_256x64.traffic.json")
     spath = os.path.join(ROOT, "paper_2407_12527_gb300", "csrc", "sweep2d.cu")
-    if WL.name == "point_source" and os.path.exists(tpath) and args.tile_g in (0, 2):
+    if WL.name == "point_source" and os.path.exists(tpath) and s["tile_g"] == 2:
         import hashlib
         with open(tpath) as f:
             tr = json.load(f)
@@ -409,6 +409,7 @@ def run_ours(args):
                 "traffic_note": "DRAM read+write bytes of one full sweep launch (ncu)",
                 "kernel": kernel_name, "launches": n_l, "avg_launch_us": avg_us,
                 "flop_per_update": fu, "sweep_avg_launch_us": 1e3 * sweep_ms / max(sweep_n, 1),
+                "tile_g": s["tile_g"],
                 "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 flop x 2070 MHz"}
 
     # end to end through the C ABI with host buffers
@@ -474,8 +475,9 @@ def main():
     ap.add_argument("--check-every", type=int, default=0,
                     help="0: device-side source-iteration loop (CUDA graph); k > 0: host loop "
                          "checking every k sweeps (profilers cannot look inside the graph loop)")
-    ap.add_argument("--tile-g", type=int, default=0,
-                    help="ordinates per sweep work item (0: library default)")
+    ap.add_argument("--tile-g", type=int, default=-1,
+                    help="ordinates per sweep work item (1, 2, 4; 0: size heuristic; "
+                         "-1: measured by the library's autotuner)")
     ap.add_argument("--only-timed", action="store_true",
                     help="run the warm-up and timed steps only (no roofline, e2e or CPU legs)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

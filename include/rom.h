@@ -80,7 +80,10 @@ typedef struct rom_options {
     int check_every; /* 0 = device-side loop (one CUDA graph with a conditional node);     */
                      /* > 0: the host reads the number of unconverged samples after every  */
                      /* check_every sweeps                                                 */
-    int tile_g;      /* 0 = automatic; else ordinates per sweep work item (1, 2 or 4)      */
+    int tile_g;      /* ordinates per sweep work item: 1, 2 or 4; 0 = chosen from the      */
+                     /* problem size; -1 = measured: at the first solve of a problem layout */
+                     /* every candidate is timed on a few sweeps and the fastest is kept   */
+                     /* (until the grid, the ordinate layout or the kernel changes)        */
     int time_kernels;/* 0; 1 records CUDA events around every sweep launch (host-driven     */
                      /* loop, check_every >= 1 is then used, 1 if it is 0) and reports the  */
                      /* summed sweep-kernel time in rom_stats.sweep_ms                     */
@@ -103,6 +106,7 @@ typedef struct rom_stats {
     int64_t sweep_launches;  /* sweep kernels timed                                       */
     double source_ms;        /* summed duration of the dense-operator contractions        */
     int64_t source_launches; /* contractions timed (dense operator only)                  */
+    int tile_g;              /* ordinates per sweep work item used by this solve          */
 } rom_stats;
 
 /* ------------------------------------------------------------- lifetime */

@@ -83,6 +83,7 @@ struct rom_ctx {
     // work items
     bool items_dirty = true;
     int G_used = 0;
+    int tuned_g = 0;  // measured choice (tile_g = -1), valid while the layout is unchanged
     std::vector<SweepItem> items;
     std::vector<int> item_begin;
     DevBuf items_dev, item_begin_dev;
@@ -170,6 +171,7 @@ void invalidate_graph(rom_ctx *ctx)
 void reset_ordinate_dependents(rom_ctx *ctx)
 {
     ctx->pmat_dirty = true;
+    ctx->tuned_g = 0;
     for (int f = 0; f < 4; ++f) ctx->inflow_ord[f].clear();
     ctx->inflow_dirty = true;
     ctx->items_dirty = true;
@@ -216,6 +218,7 @@ int set_grid_common(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3
     }
     ctx->inflow_dirty = true;
     ctx->items_dirty = true;
+    ctx->tuned_g = 0;
     ctx->solved = false;
     invalidate_graph(ctx);
     const size_t bytes = (size_t)ctx->J * ctx->NXP * sizeof(float);
@@ -240,6 +243,7 @@ int choose_g(const rom_ctx *ctx)
     const int cap = source_mode(ctx) == 0 ? 2 : 4;  // dense mode: registers for 2 ordinates
     if (ctx->opt.tile_g == 1 || ctx->opt.tile_g == 2 || ctx->opt.tile_g == 4)
         return std::min(ctx->opt.tile_g, cap);
+    if (ctx->opt.tile_g == -1 && ctx->tuned_g > 0) return std::min(ctx->tuned_g, cap);
     // largest G that still gives at least two work items per SM
     for (int G : {4, 2}) {
         if (G > cap) continue;
@@ -501,6 +505,52 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     return ROM_OK;
 }
 
+// tile_g = -1: time the sweep kernel of every candidate work-item size on the
+// current problem (three sweeps after one warm-up, from the initial source) and
+// keep the fastest.
+int autotune_g(rom_ctx *ctx)
+{
+    const int cap = source_mode(ctx) == 0 ? 2 : 4;
+    const long long cells = (long long)ctx->J * ctx->NXP;
+    const int MOMk = ctx->MOM == 0 ? 1 : ctx->MOM;
+    float best_ms = 0.f;
+    int best = 0, rc;
+    for (int G : {1, 2, 4}) {
+        if (G > cap) continue;
+        ctx->opt.tile_g = G;
+        if ((rc = build_items(ctx))) return rc;
+        if ((rc = ensure(ctx, ctx->part, ctx->items.size() * MOMk * cells * sizeof(float))))
+            return rc;
+        CK(romk::launch_init_state(ctx->S, MOMk, cells, (const float *)ctx->q.p,
+                                   (float *)ctx->phi.p, (float *)ctx->src.p, (int *)ctx->active.p,
+                                   (int *)ctx->iters.p, (int *)ctx->flags.p,
+                                   (double *)ctx->resid.p, ctx->stream));
+        if (ctx->MOM == 0)
+            CK(romk::launch_dense_init((const float *)ctx->q.p, cells, ctx->Mtot,
+                                       (float *)ctx->src_ord.p, ctx->stream));
+        const romk::SweepArgs sa = sweep_args(ctx);
+        const int L = (ctx->I + romk::kCols - 1) / romk::kCols;
+        for (int rep = 0; rep < 4; ++rep) {
+            if (rep == 1) CK(cudaEventRecord(ctx->ev0, ctx->stream));
+            CK(romk::launch_sweep2d(sa, (int)ctx->items.size(), (L + 31) / 32, G, ctx->opt.scheme,
+                                    ctx->homog, ctx->MOM, ctx->stream));
+            ++ctx->launches;
+        }
+        CK(cudaEventRecord(ctx->ev1, ctx->stream));
+        CK(cudaEventSynchronize(ctx->ev1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        if (best == 0 || ms < best_ms) {
+            best = G;
+            best_ms = ms;
+        }
+    }
+    ctx->opt.tile_g = -1;
+    ctx->tuned_g = best;
+    ctx->items_dirty = true;
+    return ROM_OK;
+}
+
 int build_graph(rom_ctx *ctx)
 {
     invalidate_graph(ctx);
@@ -626,8 +676,9 @@ int rom_set_options(rom_ctx *ctx, const rom_options *opt)
     if (opt->check_every < 0) return fail(ctx, ROM_ERR_INVALID_ARG, "check_every < 0");
     if (opt->time_kernels != 0 && opt->time_kernels != 1)
         return fail(ctx, ROM_ERR_INVALID_ARG, "time_kernels must be 0 or 1");
-    if (opt->tile_g != 0 && opt->tile_g != 1 && opt->tile_g != 2 && opt->tile_g != 4)
-        return fail(ctx, ROM_ERR_INVALID_ARG, "tile_g must be 0, 1, 2 or 4");
+    if (opt->tile_g != 0 && opt->tile_g != 1 && opt->tile_g != 2 && opt->tile_g != 4 &&
+        opt->tile_g != -1)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "tile_g must be -1, 0, 1, 2 or 4");
     if (opt->dense_source != 0 && opt->dense_source != 1)
         return fail(ctx, ROM_ERR_INVALID_ARG, "dense_source must be 0 or 1");
     if (opt->tile_g != ctx->opt.tile_g || opt->dense_source != ctx->opt.dense_source) {
@@ -983,6 +1034,7 @@ int rom_set_kernel(rom_ctx *ctx, int kind, double g, int flags)
     ctx->g = kind == ROM_KERNEL_ISO ? 0.0 : g;
     ctx->kernel_flags = flags;
     ctx->pmat_dirty = true;
+    ctx->tuned_g = 0;
     ctx->items_dirty = true;
     ctx->solved = false;
     invalidate_graph(ctx);
@@ -1035,6 +1087,13 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
         if ((rc = prepare_dense(ctx))) return rc;
         void *dense_after[] = {ctx->psi.p, ctx->src_ord.p, ctx->Amat.p, ctx->dtab.p};
         if (memcmp(dense_before, dense_after, sizeof dense_before) != 0) invalidate_graph(ctx);
+    }
+    if (ctx->opt.tile_g == -1 && ctx->tuned_g == 0) {
+        if ((rc = autotune_g(ctx))) return rc;
+        if ((rc = build_items(ctx))) return rc;
+        if ((rc = ensure(ctx, ctx->part, ctx->items.size() * MOM * cells * sizeof(float))))
+            return rc;
+        invalidate_graph(ctx);
     }
     void *after[] = {ctx->phi.p, ctx->src.p, ctx->part.p, ctx->partials.p, ctx->active.p};
     if (memcmp(before, after, sizeof before) != 0) invalidate_graph(ctx);
@@ -1136,6 +1195,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     st.sweep_launches = sweep_launches;
     st.source_ms = source_ms;
     st.source_launches = source_launches;
+    st.tile_g = ctx->G_used;
     if (device_loop) ctx->launches += (ctx->MOM == 0 ? 4LL : 3LL) * st.iterations_max;
     st.kernel_launches = ctx->launches - launches0;
     if (stats_out) *stats_out = st;

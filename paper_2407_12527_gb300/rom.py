@@ -42,7 +42,8 @@ class rom_stats(ctypes.Structure):
                 ("updates", ctypes.c_int64), ("residual_max", ctypes.c_double),
                 ("gpu_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("sweep_ms", ctypes.c_double), ("sweep_launches", ctypes.c_int64),
-                ("source_ms", ctypes.c_double), ("source_launches", ctypes.c_int64)]
+                ("source_ms", ctypes.c_double), ("source_launches", ctypes.c_int64),
+                ("tile_g", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -119,7 +119,7 @@ def test_fixed_k_parity_random_directions(rom, scheme, grid, homog):
     assert list(gpu["iters"]) == [K] * len(sets)
 
 
-@pytest.mark.parametrize("tile_g", [1, 2, 4])
+@pytest.mark.parametrize("tile_g", [-1, 1, 2, 4])
 def test_work_item_size_does_not_change_results(rom, tile_g):
     I, J = 70, 45
     bounds = (0, 1, 0, 1)
@@ -131,6 +131,8 @@ def test_work_item_size_does_not_change_results(rom, tile_g):
     ref = O.solve_xy(I, J, bounds, st, ss, q, sets, fixed_iters=5)
     for k in range(3):
         assert rel(gpu["phi"][k], ref["phi"][k]) < TOL
+    assert gpu["stats"]["tile_g"] == (tile_g if tile_g > 0 else gpu["stats"]["tile_g"])
+    assert gpu["stats"]["tile_g"] in (1, 2, 4)
 
 
 # ------------------------------------------------------ converged parity
