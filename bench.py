@@ -465,6 +465,102 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------ ROM vs DOM
+
+def run_rom_vs_dom(args):
+    """GPU time for ROM and for plain DOM to reach a relative l2 error of the scalar
+    flux of 1e-3 on the point-source problem.  Reference: the FP64 oracle with the
+    2D uniform set N = args.ref_n (4 N^2 ordinates), SI to 1e-9.  DOM: the uniform
+    set for growing N, one solve each (time = that solve).  ROM: M = 4 m ordinates
+    per sample, samples solved in batches, the running average compared after each
+    batch (time = cumulative GPU time of the batches)."""
+    import torch
+    from oracle import oracle as O
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2407_12527_gb300 import RomContext
+
+    p = W.point_source() if args.rvd_problem == "point_source" else W.example_2_1()
+    t0 = time.perf_counter()
+    ref_set = (O.quad_gauss_xy(args.ref_n) if args.ref_kind == "gauss"
+               else O.quad_uniform_xy(args.ref_n))
+    ref = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, [ref_set],
+                     tol=1e-9)["phi"][0]
+    ref_s = time.perf_counter() - t0
+    nref = float(np.linalg.norm(ref))
+
+    def rel(phi):
+        return float(np.linalg.norm(phi - ref) / nref)
+
+    ctx = RomContext(0)
+    ctx.set_grid(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q)
+    ctx.set_options(tol=TOL, tile_g=-1)
+    dom = []
+    for N in args.dom_n:
+        ctx.set_quadrature("uniform", N)
+        ctx.solve()                      # warm-up (graph capture, tuning)
+        s = ctx.solve()
+        dom.append({"N": N, "M": 4 * N * N, "ms": s["gpu_ms"], "rel_l2": rel(ctx.scalar_flux(-1))})
+    rom = []
+    for m in args.rom_m:
+        nz, nt = W.partition(m)
+        batch = args.rom_batch
+        tot_ms, acc, n = 0.0, np.zeros((p.J, p.I)), 0
+        curve = []
+        ctx.set_ordinates_seed(W.ordinate_seed(1, 7), [nz] * batch, [nt] * batch, first_sample=0)
+        ctx.solve()                      # warm-up
+        while n < args.rom_max:
+            ctx.set_ordinates_seed(W.ordinate_seed(1, 7), [nz] * batch, [nt] * batch,
+                                   first_sample=n)
+            s = ctx.solve()
+            tot_ms += s["gpu_ms"]
+            part, cnt = ctx.partial_sum()
+            acc += part
+            n += cnt
+            curve.append({"samples": n, "ms": tot_ms, "rel_l2": rel(acc / n)})
+        rom.append({"M": 4 * m, "curve": curve})
+    ctx.close()
+
+    target = args.target
+
+    def first(points, tgt=target):
+        hit = [q for q in points if q["rel_l2"] <= tgt]
+        return hit[0] if hit else None
+
+    def rom_first(tgt):
+        hits = [(first(r["curve"], tgt), r["M"]) for r in rom]
+        hits = [(h["ms"], M, h["samples"]) for h, M in hits if h]
+        return min(hits) if hits else None
+
+    dom_hit = first(dom)
+    rom_hits = [(r["M"], first(r["curve"])) for r in rom]
+    rom_best = rom_first(target)
+    coarse = {}
+    for tgt in (1e-1, 3e-2, 1e-2, 3e-3):
+        d, r = first(dom, tgt), rom_first(tgt)
+        coarse[f"{tgt:g}"] = {"dom_ms": d["ms"] if d else None, "dom_M": d["M"] if d else None,
+                              "rom_ms": r[0] if r else None, "rom_M": r[1] if r else None,
+                              "rom_samples": r[2] if r else None}
+    line = {
+        "metric": f"GPU time to relative l2 flux error {target:g}, ROM vs DOM ({p.name}, "
+                  f"{p.I}x{p.J})",
+        "unit": "ms", "higher_is_better": False, "data": "synthetic",
+        "reference": f"FP64 oracle, 2D {args.ref_kind} set N={args.ref_n} ({ref_set.M} ordinates), "
+                     f"SI to 1e-9 ({ref_s:.0f} s on the host)",
+        "dom_ms_to_target": dom_hit["ms"] if dom_hit else None,
+        "dom_M_at_target": dom_hit["M"] if dom_hit else None,
+        "rom_ms_to_target": rom_best[0] if rom_best else None,
+        "rom_M_at_target": rom_best[1] if rom_best else None,
+        "rom_samples_at_target": rom_best[2] if rom_best else None,
+        "time_to_other_targets": coarse,
+        "dom": dom,
+        "rom": [{"M": r["M"], "final": r["curve"][-1],
+                 "at_target": h} for r, (_, h) in zip(rom, rom_hits)],
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -486,8 +582,21 @@ def main():
     ap.add_argument("--workload", default="point_source",
                     choices=["point_source", "point_source_dom", "dom_small", "checkerboard",
                              "hg_disc"])
+    ap.add_argument("--rom-vs-dom", action="store_true",
+                    help="measure GPU time to a relative l2 error target, ROM vs plain DOM")
+    ap.add_argument("--target", type=float, default=1e-3)
+    ap.add_argument("--ref-n", type=int, default=100)
+    ap.add_argument("--ref-kind", default="gauss", choices=["gauss", "uniform"])
+    ap.add_argument("--rvd-problem", default="point_source", choices=["point_source", "example_2_1"])
+    ap.add_argument("--dom-n", type=int, nargs="+", default=[2, 3, 4, 6, 8, 12, 16, 24, 32])
+    ap.add_argument("--rom-m", type=int, nargs="+", default=[4, 9, 16],
+                    help="ordinate cells per quadrant (M = 4 m)")
+    ap.add_argument("--rom-batch", type=int, default=256)
+    ap.add_argument("--rom-max", type=int, default=4096)
     args = ap.parse_args()
     global WL
+    if args.rom_vs_dom:
+        return run_rom_vs_dom(args)
     WL = make_workload(args.workload)
     if args.impl == "reference":
         return run_reference(args)
