@@ -75,6 +75,14 @@ def lib() -> ctypes.CDLL:
             ctypes.c_double, dp, dp, dp, ctypes.c_int, ip, dp, dp, dp, dp, dp, ctypes.c_long,
             ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
             ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ip, dp, dp]
+        L.oracle_rom_ordinates_xyz.restype = ctypes.c_int
+        L.oracle_rom_ordinates_xyz.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, dp, dp, dp, dp]
+        L.oracle_solve_xyz.restype = ctypes.c_int
+        L.oracle_solve_xyz.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, ctypes.c_int, ip, dp, dp,
+            dp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+            dp, ip, dp, dp]
         L.oracle_max_threads.restype = ctypes.c_int
         L.oracle_max_threads.argtypes = []
         _lib = L
@@ -272,6 +280,50 @@ def solve_xy(I, J, bounds, sigma_t, sigma_s, q, ordinate_sets, *, kernel="iso", 
         raise RuntimeError("oracle: source iteration did not converge")
     if rc not in (0, -4):
         raise ValueError(f"oracle_solve_xy failed ({rc})")
+    return {"phi": phi, "iters": iters, "resid": resid, "leak": leak}
+
+
+def rom_ordinates_xyz(seed: int, sample: int, n_zeta: int, n_theta: int) -> Ordinates:
+    """3D ROM set: the X-Y set of the same draws and its mirror in zeta (8 m ordinates,
+    weights 1/(8m)); ``zeta`` holds the z direction cosine mu_z in (-1, 1)."""
+    m = n_zeta * n_theta
+    arr = [np.zeros(8 * m) for _ in range(4)]
+    rc = lib().oracle_rom_ordinates_xyz(seed, sample, n_zeta, n_theta, *(_dp(a) for a in arr))
+    if rc != 0:
+        raise ValueError(f"oracle_rom_ordinates_xyz failed ({rc})")
+    return Ordinates(*arr)
+
+
+def solve_xyz(I, J, K, bounds, sigma_t, sigma_s, q, ordinate_sets, *, scheme="dd", tol=1e-10,
+              max_iter=10000, fixed_iters=0, inflow=None, n_threads=0,
+              allow_not_converged=False):
+    """3D source iteration, isotropic scattering.  bounds = (x_L, x_R, y_B, y_T, z_B, z_T);
+    sigma_t, sigma_s, q are [K, J, I]; ordinate sets carry mu_z in ``zeta``; inflow is
+    None or isotropic face values [x_L: K*J][x_R: K*J][y_B: K*I][y_T: K*I][z_B: J*I][z_T: J*I].
+    Returns dict(phi [n_samples, K, J, I], iters, resid, leak)."""
+    b = _f64(bounds)
+    st, ss, qq = (_f64(np.broadcast_to(a, (K, J, I))) for a in (sigma_t, sigma_s, q))
+    ns = len(ordinate_sets)
+    mps = np.array([o.M for o in ordinate_sets], dtype=np.int32)
+    cat = [_f64(np.concatenate([getattr(o, f) for o in ordinate_sets])) if ns else np.zeros(1)
+           for f in ("c", "s", "zeta", "w")]
+    infl = None if inflow is None else _f64(inflow)
+    if infl is not None:
+        assert infl.size == 2 * K * J + 2 * K * I + 2 * J * I
+    phi = np.zeros((ns, K, J, I))
+    iters = np.zeros(ns, dtype=np.int32)
+    resid = np.zeros(ns)
+    leak = np.zeros(ns)
+    ip = ctypes.POINTER(ctypes.c_int)
+    rc = lib().oracle_solve_xyz(
+        I, J, K, _dp(b), _dp(st), _dp(ss), _dp(qq), ns, mps.ctypes.data_as(ip),
+        *(_dp(a) for a in cat), _dp(infl) if infl is not None else None, SCHEMES[scheme],
+        float(tol), int(max_iter), int(fixed_iters), int(n_threads), _dp(phi),
+        iters.ctypes.data_as(ip), _dp(resid), _dp(leak))
+    if rc == -4 and not allow_not_converged:
+        raise RuntimeError("oracle: source iteration did not converge")
+    if rc not in (0, -4):
+        raise ValueError(f"oracle_solve_xyz failed ({rc})")
     return {"phi": phi, "iters": iters, "resid": resid, "leak": leak}
 
 

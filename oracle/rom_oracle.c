@@ -1,7 +1,8 @@
 /*
  * rom_oracle.c -- plain FP64 CPU oracle for the Random Ordinate Method (ROM)
  * of Li, Tang & Yang, "A random ordinate method for mitigating the ray effect
- * in radiative transport equation simulations" (arXiv 2407.12527), X-Y geometry.
+ * in radiative transport equation simulations" (arXiv 2407.12527), X-Y and
+ * x-y-z geometry.
  *
  * TEST INFRASTRUCTURE ONLY.  The test-suite, the smoke check and the CPU
  * baseline leg of the benchmark are the only users of this file.  The CUDA
@@ -27,6 +28,10 @@
  *   - Scattering source sigma_S * sum_l' w_l' P(u_l', u_l) psi_l' + q with
  *     P = 1 (isotropic), P = 1 + g cos(xi) (eq. anisotropic kernel) or the
  *     Henyey-Greenstein kernel, optionally row-normalised (Remark, Sec. 3.1).
+ *   - 3D (x-y-z) geometry, in which eq. (equ_1) is posed (Sec. 1) though the
+ *     paper tests only slab and X-Y: the X-Y set of the same draws mirrored in zeta (8 m ordinates on the whole
+ *     sphere, weights 1/(8 m) each), DD or step on a uniform box grid with
+ *     six inflow faces, isotropic scattering only.
  *
  * Readings of points the paper leaves open:
  *   - cell centres are x_L + (i + 1/2) dx, i = 0..I-1 (the grid definition in
@@ -416,4 +421,187 @@ int oracle_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ============================================================ 3D (x-y-z) */
+
+/*
+ * ROM ordinates in 3D (the RTE of Sec. 1 posed for z in R^3): the draws and
+ * the first-quadrant partition of the X-Y construction (Sec. 4.2) give the
+ * upper-hemisphere points (c, s, zeta), zeta in (0, 1); their mirror images
+ * (c, s, -zeta) complete the sphere, 8 octants of m points each, every weight
+ * |S_l| / |S| = 1 / (8 m).  Output: the 4 m upper points in the X-Y order, then
+ * their mirrors in the same order.  dirs are written as (c, s, mu_z).
+ */
+int oracle_rom_ordinates_xyz(uint64_t seed, int sample, int n_zeta, int n_theta, double *c,
+                             double *s, double *mu_z, double *w)
+{
+    const int m = n_zeta * n_theta;
+    int rc = oracle_rom_ordinates_xy(seed, sample, n_zeta, n_theta, c, s, mu_z, w);
+    if (rc != ORACLE_OK) return rc;
+    for (int l = 0; l < 4 * m; ++l) {
+        c[4 * m + l] = c[l];
+        s[4 * m + l] = s[l];
+        mu_z[4 * m + l] = -mu_z[l];
+        w[l] = 1.0 / (8.0 * m);
+        w[4 * m + l] = 1.0 / (8.0 * m);
+    }
+    return ORACLE_OK;
+}
+
+typedef struct {
+    int I, J, K;
+    double dx, dy, dz;
+} grid3_t;
+
+/*
+ * Diamond-difference (or step) sweep of one 3D ordinate (c, s, mu_z) in upwind
+ * order: per cell, with a = f|c|/dx, b = f|s|/dy, e = f|mu_z|/dz (f = 2 for DD,
+ * 1 for step), psi_c = (src + a psi_xin + b psi_yin + e psi_zin) / (sigma_T + a + b + e),
+ * DD outflows 2 psi_c - inflow, step outflows psi_c.  Inflow: isotropic face
+ * values, layout [x_L: K*J][x_R: K*J][y_B: K*I][y_T: K*I][z_B: J*I][z_T: J*I]
+ * ([k][j], [k][i], [j][i]); NULL = vacuum.  Returns the net boundary outflow.
+ */
+static double sweep_ordinate3(const grid3_t *G, const double *sigma_t, const double *src,
+                              double c, double s, double mz, int scheme, const double *inflow,
+                              double *psi, double *psi_y /* [I] */, double *psi_z /* [J*I] */)
+{
+    const int I = G->I, J = G->J, K = G->K;
+    const double f = (scheme == SCHEME_DD) ? 2.0 : 1.0;
+    const double mu = fabs(c), eta = fabs(s), xi = fabs(mz);
+    const double ax = f * mu / G->dx, by = f * eta / G->dy, ez = f * xi / G->dz;
+    const int xpos = (c >= 0.0), ypos = (s >= 0.0), zpos = (mz >= 0.0);
+    const size_t fx = (size_t)K * J, fy = (size_t)K * I;
+    const size_t o_xl = 0, o_xr = fx, o_yb = 2 * fx, o_yt = 2 * fx + fy, o_zb = 2 * fx + 2 * fy,
+                 o_zt = 2 * fx + 2 * fy + (size_t)J * I;
+    double leak = 0.0;
+    const double aX = mu * G->dy * G->dz, aY = eta * G->dx * G->dz, aZ = xi * G->dx * G->dy;
+
+    for (int j = 0; j < J; ++j)
+        for (int i = 0; i < I; ++i) {
+            double in = inflow ? inflow[(zpos ? o_zb : o_zt) + (size_t)j * I + i] : 0.0;
+            psi_z[(size_t)j * I + i] = in;
+            leak -= aZ * in;
+        }
+    for (int kk = 0; kk < K; ++kk) {
+        const int k = zpos ? kk : K - 1 - kk;
+        for (int i = 0; i < I; ++i) {
+            double in = inflow ? inflow[(ypos ? o_yb : o_yt) + (size_t)k * I + i] : 0.0;
+            psi_y[i] = in;
+            leak -= aY * in;
+        }
+        for (int jj = 0; jj < J; ++jj) {
+            const int j = ypos ? jj : J - 1 - jj;
+            double psi_x = inflow ? inflow[(xpos ? o_xl : o_xr) + (size_t)k * J + j] : 0.0;
+            leak -= aX * psi_x;
+            for (int ii = 0; ii < I; ++ii) {
+                const int i = xpos ? ii : I - 1 - ii;
+                const size_t cell = ((size_t)k * J + j) * I + i;
+                double *pz = &psi_z[(size_t)j * I + i];
+                double pc = (src[cell] + ax * psi_x + by * psi_y[i] + ez * *pz) /
+                            (sigma_t[cell] + ax + by + ez);
+                psi[cell] = pc;
+                if (scheme == SCHEME_DD) {
+                    psi_x = 2.0 * pc - psi_x;
+                    psi_y[i] = 2.0 * pc - psi_y[i];
+                    *pz = 2.0 * pc - *pz;
+                } else {
+                    psi_x = pc;
+                    psi_y[i] = pc;
+                    *pz = pc;
+                }
+            }
+            leak += aX * psi_x;
+        }
+        for (int i = 0; i < I; ++i) leak += aY * psi_y[i];
+    }
+    for (size_t n = 0; n < (size_t)J * I; ++n) leak += aZ * psi_z[n];
+    return leak;
+}
+
+/*
+ * Source iteration in 3D with isotropic scattering (S = sigma_S phi + q), per
+ * ordinate set, on the I x J x K grid of [xl,xr] x [yb,yt] x [zb,zt]; arrays
+ * [K][J][I] (x fastest).  Arguments as oracle_solve_xy; dirs (c, s, mu_z).
+ */
+int oracle_solve_xyz(int I, int J, int K, const double *bounds /* xl xr yb yt zb zt */,
+                     const double *sigma_t, const double *sigma_s, const double *q, int n_samples,
+                     const int *m_per_sample, const double *c, const double *s, const double *mz,
+                     const double *w, const double *inflow, int scheme, double tol, int max_iter,
+                     int fixed_iters, int n_threads, double *phi_out, int *iters_out,
+                     double *resid_out, double *leak_out)
+{
+    if (I < 1 || J < 1 || K < 1 || n_samples < 0) return ORACLE_EINVAL;
+    if (!(bounds[1] > bounds[0]) || !(bounds[3] > bounds[2]) || !(bounds[5] > bounds[4]))
+        return ORACLE_EINVAL;
+    if (scheme != SCHEME_DD && scheme != SCHEME_STEP) return ORACLE_EINVAL;
+    if (fixed_iters <= 0 && max_iter < 1) return ORACLE_EINVAL;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    const grid3_t G = {I, J, K, (bounds[1] - bounds[0]) / I, (bounds[3] - bounds[2]) / J,
+                       (bounds[5] - bounds[4]) / K};
+    const size_t nc = (size_t)I * J * K;
+    int status = ORACLE_OK;
+    long offset = 0;
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    for (int smp = 0; smp < n_samples; ++smp) {
+        const int M = m_per_sample[smp];
+        double *phi = phi_out + (size_t)smp * nc;
+        double *phi_new = calloc(nc, sizeof(double));
+        double *part = calloc(nc * (size_t)nthr, sizeof(double));
+        double *psi_tmp = malloc(nc * (size_t)nthr * sizeof(double));
+        double *psi_y = malloc((size_t)I * nthr * sizeof(double));
+        double *psi_z = malloc((size_t)I * J * nthr * sizeof(double));
+        double *src = malloc(nc * sizeof(double));
+        double *leak_l = malloc((size_t)(M > 0 ? M : 1) * sizeof(double));
+        if (!phi_new || !part || !psi_tmp || !psi_y || !psi_z || !src || !leak_l) {
+            free(phi_new); free(part); free(psi_tmp); free(psi_y); free(psi_z); free(src); free(leak_l);
+            return ORACLE_ENOMEM;
+        }
+        memset(phi, 0, nc * sizeof(double));
+        int it = 0;
+        double resid = INFINITY, leak = 0.0;
+        const int limit = fixed_iters > 0 ? fixed_iters : max_iter;
+        while (it < limit) {
+            for (size_t n = 0; n < nc; ++n) src[n] = sigma_s[n] * phi[n] + q[n];
+            memset(part, 0, nc * (size_t)nthr * sizeof(double));
+#pragma omp parallel for schedule(static)
+            for (int l = 0; l < M; ++l) {
+                int t = 0;
+#ifdef _OPENMP
+                t = omp_get_thread_num();
+#endif
+                double *psi = psi_tmp + (size_t)t * nc;
+                leak_l[l] = sweep_ordinate3(&G, sigma_t, src, c[offset + l], s[offset + l],
+                                            mz[offset + l], scheme, inflow, psi,
+                                            psi_y + (size_t)t * I, psi_z + (size_t)t * I * J);
+                double *pt = part + (size_t)t * nc;
+                for (size_t n = 0; n < nc; ++n) pt[n] += w[offset + l] * psi[n];
+            }
+            for (size_t n = 0; n < nc; ++n) {
+                double acc = 0.0;
+                for (int t = 0; t < nthr; ++t) acc += part[(size_t)t * nc + n];
+                phi_new[n] = acc;
+            }
+            leak = 0.0;
+            for (int l = 0; l < M; ++l) leak += w[offset + l] * leak_l[l];
+            resid = l2diff_rel(phi_new, phi, nc);
+            memcpy(phi, phi_new, nc * sizeof(double));
+            ++it;
+            if (fixed_iters <= 0 && resid < tol) break;
+        }
+        if (fixed_iters <= 0 && !(resid < tol)) status = ORACLE_ENOTCONV;
+        if (iters_out) iters_out[smp] = it;
+        if (resid_out) resid_out[smp] = resid;
+        if (leak_out) leak_out[smp] = leak;
+        free(phi_new); free(part); free(psi_tmp); free(psi_y); free(psi_z); free(src); free(leak_l);
+        offset += M;
+    }
+    return status;
 }

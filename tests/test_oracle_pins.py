@@ -422,3 +422,161 @@ def test_metrics():
     assert O.rom_error(samples, ref) == pytest.approx(
         np.mean([np.sqrt(np.mean((s - ref) ** 2)) for s in samples]))
     assert O.mc_error(samples, ref, 2) == pytest.approx(O.l2_xy(samples[:2].mean(0), ref))
+
+
+# ================================================================ 3D (x-y-z)
+
+def _random_sphere(M, seed, weights="random"):
+    rng = np.random.default_rng(seed)
+    mz = rng.uniform(-1.0, 1.0, size=M)
+    th = rng.uniform(0.0, 2.0 * np.pi, size=M)
+    rho = np.sqrt(1.0 - mz * mz)
+    w = rng.uniform(0.5, 1.5, size=M) if weights == "random" else np.ones(M)
+    return O.Ordinates(rho * np.cos(th), rho * np.sin(th), mz, w / w.sum())
+
+
+@pytest.mark.parametrize("scheme", ["dd", "step"])
+@pytest.mark.parametrize("axis", ["x", "z"])
+def test_3d_pure_absorber_axis_closed_form(scheme, axis):
+    """3D, one axis-aligned ordinate in a pure absorber: the discrete closed form
+    (q/sigma_T)(1 - r^k) of the edge values along that axis (cf. the 2D pin)."""
+    I, J, K = (30, 2, 3) if axis == "x" else (2, 3, 30)
+    sig, q, mu = 1.3, 0.7, 0.6
+    L = 1.5
+    bounds = (0.0, L if axis == "x" else 1.0, 0.0, 1.0, 0.0, L if axis == "z" else 1.0)
+    n = I if axis == "x" else K
+    for sign in (1.0, -1.0):
+        d = [sign * mu, 0.0, 0.0] if axis == "x" else [0.0, 0.0, sign * mu]
+        o = O.Ordinates([d[0]], [d[1]], [d[2]], [1.0])
+        phi = O.solve_xyz(I, J, K, bounds, sig, 0.0, q, [o], scheme=scheme,
+                          fixed_iters=1)["phi"][0]
+        tau = sig * (L / n) / mu
+        r = (2 - tau) / (2 + tau) if scheme == "dd" else 1.0 / (1.0 + tau)
+        edge = q / sig * (1.0 - r ** np.arange(n + 1))
+        centre = 0.5 * (edge[:-1] + edge[1:]) if scheme == "dd" else edge[1:]
+        if sign < 0:
+            centre = centre[::-1]
+        line = phi[0, 0, :] if axis == "x" else phi[:, 0, 0]
+        np.testing.assert_allclose(line, centre, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("scheme", ["dd", "step"])
+def test_3d_equilibrium_inflow(scheme):
+    I, J, K, st, ss, q = 5, 4, 6, 2.0, 1.2, 0.9
+    val = q / (st - ss)
+    infl = np.full(2 * K * J + 2 * K * I + 2 * J * I, val)
+    sets = [O.rom_ordinates_xyz(3, 0, 2, 2), _random_sphere(7, 8)]
+    r = O.solve_xyz(I, J, K, (0, 1, 0, 1.3, 0, 0.7), st, ss, q, sets, scheme=scheme, tol=1e-14,
+                    inflow=infl)
+    np.testing.assert_allclose(r["phi"], val, rtol=1e-12)
+
+
+@pytest.mark.parametrize("scheme", ["dd", "step"])
+def test_3d_particle_balance(scheme):
+    I, J, K = 6, 5, 4
+    bounds = (0.0, 1.2, -0.1, 0.9, 0.0, 0.8)
+    dV = (1.2 / I) * (1.0 / J) * (0.8 / K)
+    rng = np.random.default_rng(12)
+    st = rng.uniform(0.5, 3.0, size=(K, J, I))
+    ss = st * rng.uniform(0, 0.8, size=(K, J, I))
+    q = rng.uniform(0, 2.0, size=(K, J, I))
+    infl = rng.uniform(0, 1.0, size=2 * K * J + 2 * K * I + 2 * J * I)
+    o = _random_sphere(9, 13)
+    rk = O.solve_xyz(I, J, K, bounds, st, ss, q, [o], scheme=scheme, fixed_iters=3, inflow=infl)
+    rk1 = O.solve_xyz(I, J, K, bounds, st, ss, q, [o], scheme=scheme, fixed_iters=2, inflow=infl)
+    lhs = rk["leak"][0] + np.sum(st * rk["phi"][0]) * dV
+    rhs = np.sum(ss * rk1["phi"][0] + q) * dV
+    assert abs(lhs - rhs) < 1e-12 * abs(rhs)
+
+
+@pytest.mark.parametrize("scheme", ["dd", "step"])
+def test_3d_bruteforce_dense_solve(scheme):
+    """Independent assembly of the 3D cell balance + closures + inflow (isotropic
+    scattering, unequal weights), solved by LU, equals converged 3D SI."""
+    I, J, K = 3, 2, 2
+    bounds = (0.0, 1.0, 0.0, 0.7, 0.0, 0.5)
+    dx, dy, dz = 1.0 / I, 0.7 / J, 0.5 / K
+    rng = np.random.default_rng(31)
+    st = rng.uniform(0.5, 2.0, size=(K, J, I))
+    ss = st * rng.uniform(0, 0.7, size=(K, J, I))
+    q = rng.uniform(0, 1.0, size=(K, J, I))
+    nf = 2 * K * J + 2 * K * I + 2 * J * I
+    infl = rng.uniform(0, 1.0, size=nf)
+    o = _random_sphere(6, 32)
+    M = o.M
+    nc = I * J * K
+    nxe, nye, nze = (I + 1) * J * K, I * (J + 1) * K, I * J * (K + 1)
+    per = nc + nxe + nye + nze
+    A = np.zeros((M * per, M * per))
+    b = np.zeros(M * per)
+    cen = lambda l, i, j, k: l * per + (k * J + j) * I + i
+    xe = lambda l, i, j, k: l * per + nc + (k * J + j) * (I + 1) + i
+    ye = lambda l, i, j, k: l * per + nc + nxe + (k * (J + 1) + j) * I + i
+    ze = lambda l, i, j, k: l * per + nc + nxe + nye + (k * J + j) * I + i
+    oxl, oxr, oyb, oyt = 0, K * J, 2 * K * J, 2 * K * J + K * I
+    ozb, ozt = 2 * K * J + 2 * K * I, 2 * K * J + 2 * K * I + J * I
+    row = 0
+    for l in range(M):
+        c, s, m = o.c[l], o.s[l], o.zeta[l]
+        for k in range(K):
+            for j in range(J):
+                for i in range(I):
+                    A[row, xe(l, i + 1, j, k)] += c / dx
+                    A[row, xe(l, i, j, k)] -= c / dx
+                    A[row, ye(l, i, j + 1, k)] += s / dy
+                    A[row, ye(l, i, j, k)] -= s / dy
+                    A[row, ze(l, i, j, k + 1)] += m / dz
+                    A[row, ze(l, i, j, k)] -= m / dz
+                    A[row, cen(l, i, j, k)] += st[k, j, i]
+                    for lp in range(M):
+                        A[row, cen(lp, i, j, k)] -= ss[k, j, i] * o.w[lp]
+                    b[row] = q[k, j, i]
+                    row += 1
+                    pairs = ((xe(l, i, j, k), xe(l, i + 1, j, k), c),
+                             (ye(l, i, j, k), ye(l, i, j + 1, k), s),
+                             (ze(l, i, j, k), ze(l, i, j, k + 1), m))
+                    for lo, hi, d in pairs:
+                        if scheme == "dd":
+                            A[row, cen(l, i, j, k)] = 1.0
+                            A[row, lo] = A[row, hi] = -0.5
+                        else:
+                            A[row, hi if d >= 0 else lo] = 1.0
+                            A[row, cen(l, i, j, k)] = -1.0
+                        row += 1
+        for k in range(K):
+            for j in range(J):
+                A[row, xe(l, 0, j, k) if c >= 0 else xe(l, I, j, k)] = 1.0
+                b[row] = infl[(oxl if c >= 0 else oxr) + k * J + j]
+                row += 1
+            for i in range(I):
+                A[row, ye(l, i, 0, k) if s >= 0 else ye(l, i, J, k)] = 1.0
+                b[row] = infl[(oyb if s >= 0 else oyt) + k * I + i]
+                row += 1
+        for j in range(J):
+            for i in range(I):
+                A[row, ze(l, i, j, 0) if m >= 0 else ze(l, i, j, K)] = 1.0
+                b[row] = infl[(ozb if m >= 0 else ozt) + j * I + i]
+                row += 1
+    assert row == M * per
+    x = np.linalg.solve(A, b)
+    want = sum(o.w[l] * x[l * per:l * per + nc].reshape(K, J, I) for l in range(M))
+    got = O.solve_xyz(I, J, K, bounds, st, ss, q, [o], scheme=scheme, tol=1e-15, max_iter=500,
+                      inflow=infl, allow_not_converged=True)["phi"][0]
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-13)
+
+
+def test_3d_rom_set_mirror_symmetry_and_moments():
+    """The 3D set is closed under c -> -c, s -> -s and mu_z -> -mu_z, so each sample's
+    phi of a problem symmetric in x, y and z has the three mirrors; its weighted
+    moments are those of the sphere on average (E sum w mu_z^2 = 1/3)."""
+    n = 10
+    src = np.zeros((n, n, n))
+    src[3:7, 3:7, 3:7] = 1.0
+    o = O.rom_ordinates_xyz(21, 0, 2, 2)
+    phi = O.solve_xyz(n, n, n, (0, 1, 0, 1, 0, 1), 1.0, 0.5, src, [o], tol=1e-13)["phi"][0]
+    tol = 1e-12 * phi.max()
+    for ax in range(3):
+        np.testing.assert_allclose(phi, np.flip(phi, axis=ax), rtol=1e-11, atol=tol)
+    vals = np.array([np.sum(q.w * q.zeta ** 2) for q in
+                     (O.rom_ordinates_xyz(5, k, 1, 2) for k in range(2000))])
+    assert abs(vals.mean() - 1 / 3) < 5 * vals.std() / np.sqrt(vals.size)
