@@ -5,7 +5,8 @@
  *     u . grad psi + sigma_T psi = sigma_S fint_S P(u', u) psi(u') du' + q,
  *     psi = psi_Gamma on the inflow boundary (u . n < 0),
  * (Li, Tang & Yang, arXiv 2407.12527, Sec. 1, eq. equ_1 / equ_1_bc) in X-Y
- * geometry by the Random Ordinate Method (Sec. 3.1): for each of several
+ * geometry, or in 3D (x-y-z) geometry where eq. equ_1 is posed (the paper
+ * tests only slab and X-Y), by the Random Ordinate Method (Sec. 3.1): for each of several
  * ordinate sets ("samples") it solves the discrete ordinate system of
  * eq. (equ_random) with inflow eq. (equ_random_bd), discretised in space by
  * diamond difference on a uniform Cartesian grid with cell-centred unknowns
@@ -16,8 +17,9 @@
  * Conventions shared by every call:
  *   - A context is used by one host thread at a time.  All device work of a
  *     context is issued on its stream (rom_set_stream), in order.
- *   - Cell arrays are [J][I] (2D), x fastest, cell (i, j) centred at
- *     (x_L + (i + 1/2) dx, y_B + (j + 1/2) dy), i = 0..I-1, j = 0..J-1.
+ *   - Cell arrays are [J][I] (2D) or [K][J][I] (3D), x fastest, cell (i, j, k)
+ *     centred at (x_L + (i + 1/2) dx, y_B + (j + 1/2) dy, z_B + (k + 1/2) dz),
+ *     i = 0..I-1, j = 0..J-1, k = 0..K-1.
  *   - Input buffers are read during the call and never kept: the caller keeps
  *     ownership and may reuse them as soon as the call returns (device inputs
  *     of the *_device calls are copied on the context stream, and the call
@@ -27,7 +29,10 @@
  *     error inside a call is reported as ROM_ERR_CUDA and leaves the context
  *     in need of rom_destroy.
  *   - Arithmetic: sweeps and source updates in FP32, the source-iteration
- *     residual norms and the sample average in FP64.
+ *     residual norms and the sample average in FP64.  3D sweeps add each
+ *     ordinate's contribution to the scalar flux with atomic FP32 vector
+ *     additions, so the order of the terms, and the last bits of phi, can
+ *     differ from run to run.
  */
 #ifndef ROM_GB300_H
 #define ROM_GB300_H
@@ -47,7 +52,7 @@ extern "C" {
 #define ROM_ERR_NOT_CONVERGED (-4) /* some sample reached max_iter above tol                   */
 #define ROM_ERR_DIVERGED (-5)      /* a residual became NaN/Inf                                */
 #define ROM_ERR_STATE (-6)         /* call made before the data it needs was set               */
-#define ROM_ERR_UNSUPPORTED (-7)   /* option not built (e.g. dim = 3)                          */
+#define ROM_ERR_UNSUPPORTED (-7)   /* combination not built (e.g. an anisotropic kernel in 3D) */
 
 /* --------------------------------------------------------------- choices */
 #define ROM_SCHEME_DD 0   /* diamond difference (Sec. 2)                      */
@@ -64,6 +69,8 @@ extern "C" {
 #define ROM_FACE_XR 1 /* x = x_R */
 #define ROM_FACE_YB 2 /* y = y_B */
 #define ROM_FACE_YT 3 /* y = y_T */
+#define ROM_FACE_ZB 4 /* z = z_B (3D) */
+#define ROM_FACE_ZT 5 /* z = z_T (3D) */
 
 #define ROM_QUAD_UNIFORM 0    /* 2D uniform set, Appendix A eq. (uniform2D): n1 = N, M = 4 N^2      */
 #define ROM_QUAD_GAUSS 1      /* 2D Gaussian set, Appendix A: n1 = N, M = 2 N (N + 1)               */
@@ -131,14 +138,17 @@ int rom_set_options(rom_ctx *ctx, const rom_options *opt);
 
 /* ---------------------------------------------------------------- problem */
 
-/* Grid and coefficients (Sec. 1 eq. equ_1; Sec. 2 grid).  dim must be 2.
- * n[0] = I, n[1] = J (>= 1 each); lo = (x_L, y_B), hi = (x_R, y_T) with hi > lo.
- * sigma_t, sigma_s, q: host FP64 [J][I] with 0 <= sigma_S < sigma_T and q >= 0
- * (the paper's hypotheses, Sec. 1).  Resets any inflow to vacuum. */
+/* Grid and coefficients (Sec. 1 eq. equ_1; Sec. 2 grid).  dim = 2: n[0] = I,
+ * n[1] = J (>= 1 each, I <= 2048), lo = (x_L, y_B), hi = (x_R, y_T), n[2], lo[2],
+ * hi[2] unused; dim = 3: also n[2] = K, lo[2] = z_B, hi[2] = z_T (each size
+ * 1..4096).  hi > lo on every axis.  sigma_t, sigma_s, q: host FP64 [J][I] or
+ * [K][J][I] with 0 <= sigma_S < sigma_T and q >= 0 (the paper's hypotheses,
+ * Sec. 1).  Resets any inflow to vacuum.  3D grids support the isotropic kernel
+ * (rom_solve returns ROM_ERR_UNSUPPORTED for any other). */
 int rom_set_grid(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3], const double hi[3],
                  const double *sigma_t, const double *sigma_s, const double *q);
 
-/* As rom_set_grid with FP32 device arrays [J][I] on the context's device; they
+/* As rom_set_grid with FP32 device arrays [J][I] ([K][J][I]) on the context's device; they
  * are copied on the context stream and may be reused once the call returns.
  * The hypotheses on the coefficients are checked on the device. */
 int rom_set_grid_device(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3],
@@ -146,7 +156,9 @@ int rom_set_grid_device(rom_ctx *ctx, int dim, const int64_t n[3], const double 
                         const float *q);
 
 /* Isotropic inflow psi_Gamma on one face (eq. equ_1_bc): host FP64 values per
- * face cell (J for the x faces, I for the y faces), >= 0; NULL = vacuum. */
+ * face cell, >= 0; NULL = vacuum.  2D: J values for the x faces, I for the y
+ * faces.  3D (faces 0..5): [K][J] for the x faces, [K][I] for the y faces,
+ * [J][I] for the z faces. */
 int rom_set_inflow_isotropic(rom_ctx *ctx, int face, const double *psi_face);
 
 /* Inflow per ordinate on one face (eq. equ_random_bd): host FP64
@@ -159,7 +171,8 @@ int rom_set_inflow_ordinates(rom_ctx *ctx, int face, const double *psi);
  * m_per_sample[s] >= 1 ordinates each, concatenated.  dirs is host FP64
  * [sum M][3] = (c, s, zeta) with c^2 + s^2 + zeta^2 = 1 (to 1e-6), weights
  * [sum M] > 0.  Each ordinate sweeps from the x_L side if c >= 0 (else x_R) and
- * from the y_B side if s >= 0 (else y_T). */
+ * from the y_B side if s >= 0 (else y_T); on a 3D grid zeta is the direction
+ * cosine mu_z, and the sweep starts from z_B if mu_z >= 0 (else z_T). */
 int rom_set_ordinates(rom_ctx *ctx, int n_samples, const int32_t *m_per_sample,
                       const double *dirs, const double *weights);
 
@@ -176,6 +189,14 @@ int rom_set_ordinates_seed(rom_ctx *ctx, uint64_t seed, int n_samples, const int
                            const int32_t *n_theta);
 int rom_set_ordinates_seed_offset(rom_ctx *ctx, uint64_t seed, int first_sample, int n_samples,
                                   const int32_t *n_zeta, const int32_t *n_theta);
+
+/* Random ordinate sets on the whole sphere, for 3D grids (eq. equ_1 posed in
+ * R^3; Sec. 3.1 construction): the 4 m points of rom_set_ordinates_seed_offset
+ * (same counters, same order) followed by their mirror images (c, s, -zeta),
+ * 8 m = 8 n_zeta n_theta ordinates per sample, one per octant cell of equal
+ * area, every weight 1 / (8 m).  Directions are (c, s, mu_z). */
+int rom_set_ordinates_seed_xyz(rom_ctx *ctx, uint64_t seed, int first_sample, int n_samples,
+                               const int32_t *n_zeta, const int32_t *n_theta);
 
 /* One deterministic DOM set as a single sample (Appendix A): see ROM_QUAD_*. */
 int rom_set_quadrature(rom_ctx *ctx, int kind, int n1, int n2);
@@ -206,17 +227,17 @@ int rom_set_kernel(rom_ctx *ctx, int kind, double g, int flags);
 int rom_solve(rom_ctx *ctx, rom_stats *stats_out);
 
 /* Scalar flux phi = sum_l w_l psi_l at the cell centres (Sec. 2) into host FP64
- * [J][I]: sample >= 0 one sample, sample = -1 the average over samples. */
+ * [J][I] ([K][J][I]): sample >= 0 one sample, sample = -1 the average over samples. */
 int rom_get_scalar_flux(rom_ctx *ctx, int sample, double *out);
 
-/* As rom_get_scalar_flux into a device FP64 buffer [J][I] (written on the
+/* As rom_get_scalar_flux into a device FP64 buffer [J][I] or [K][J][I] (written on the
  * context stream; the call returns after enqueueing the copy). */
 int rom_get_scalar_flux_device(rom_ctx *ctx, int sample, double *out);
 
 /* Sweeps each sample took and its last relative change (host arrays [n_samples]). */
 int rom_get_iterations(rom_ctx *ctx, int32_t *iters, double *residuals);
 
-/* Sum over this context's samples of phi (FP64 [J][I]) and their count, for
+/* Sum over this context's samples of phi (FP64 [J][I] or [K][J][I]) and their count, for
  * combining runs over disjoint sample ranges (rom_set_ordinates_seed_offset). */
 int rom_get_partial_sum(rom_ctx *ctx, double *sum_out, int64_t *count_out);
 

@@ -7,7 +7,9 @@
 // cell, (c, s) = sqrt(1 - zeta^2)(cos theta, sin theta), and the other three
 // quadrants follow from the reflections of eq. (2Dordinates_symmetry), which
 // for (c, s) are the sign changes (-c, s), (-c, -s), (c, -s).  Weights are
-// |S_l| / |S| = 1 / (4 n_zeta n_theta) (eq. wl).  The uniform numbers come from
+// |S_l| / |S| = 1 / (4 n_zeta n_theta) (eq. wl).  3D sets add the mirror image
+// (c, s, -zeta) of each of those 4 m points (the lower hemisphere), weights
+// 1 / (8 n_zeta n_theta).  The uniform numbers come from
 // SplitMix64 (Steele, Lea & Flood 2014): the n-th output of seed k is
 // mix(k + (n + 1) * 0x9E3779B97F4A7C15), its top 53 bits scaled by 2^-53.
 //
@@ -62,19 +64,22 @@ __global__ void ordgen_kernel(const OrdGenArgs A)
     const double rho = sqrt(1.0 - zeta * zeta);
     double sn, cs;
     sincos(theta, &sn, &cs);
-    const double c = rho * cs, sv = rho * sn, w = 1.0 / (4.0 * m);
+    const double c = rho * cs, sv = rho * sn, w = 1.0 / ((A.octants ? 8.0 : 4.0) * m);
     const long long base = A.ord_off[s] + l0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const double cq = (q == 1 || q == 2) ? -c : c;
-        const double sq = (q >= 2) ? -sv : sv;
+    for (int q = 0; q < 8; ++q) {
+        if (q >= 4 && !A.octants) break;
+        const double cq = (q == 1 || q == 2 || q == 5 || q == 6) ? -c : c;
+        const double sq = ((q & 3) >= 2) ? -sv : sv;
+        const double zq = q >= 4 ? -zeta : zeta;  // 3D: the mirror image in zeta
         const long long o = base + (long long)q * m;
         A.c64[o] = cq;
         A.s64[o] = sq;
-        A.z64[o] = zeta;
+        A.z64[o] = zq;
         A.w64[o] = w;
         A.c32[o] = (float)cq;
         A.s32[o] = (float)sq;
+        A.z32[o] = (float)zq;
         A.w32[o] = (float)w;
     }
 }

@@ -56,8 +56,20 @@ __global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
         ld8_volatile(phi + v, old);
         ldg8(A.sigma_s + v, ss);
         ldg8(A.q + v, qq);
-        // items in batches of eight independent loads, summed in item order
         int it = ib;
+        if (A.zero_part) {  // the sample's one accumulated array, cleared for the next sweep
+            float *p = const_cast<float *>(A.part) + (long long)ib * cells + v;
+            float t[8], zero[8];
+            ld8_volatile(p, t);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                acc[0][e] = t[e];
+                zero[e] = 0.f;
+            }
+            stg8(p, zero);
+            it = ie;
+        }
+        // items in batches of eight independent loads, summed in item order
         for (; it + 8 <= ie; it += 8)
 #pragma unroll
             for (int m = 0; m < MOM; ++m) {

@@ -4,7 +4,8 @@
 // validates arguments, lays data out in device memory and orders launches.
 //
 // Source iteration (Sec. 3.2, eq. psiexpansion), per sweep k:
-//   sweep    (K1)  every active sample: moments of L^{-1}(scatter(psi^{k-1}) + q)
+//   sweep    (K1; K9 on 3D grids) every active sample: moments of
+//                  L^{-1}(scatter(psi^{k-1}) + q)
 //   combine  (K2)  phi^k per sample, next source, FP64 residual partials
 //   finalize (K5)  ||phi^k - phi^{k-1}|| / ||phi^k|| per sample, stop flags
 // then the FP64 sample average (K6).  The loop runs either on the device (a
@@ -50,17 +51,19 @@ struct rom_ctx {
     std::string err;
     rom_options opt{};
 
-    // grid
+    // grid (dim 3: K planes; cell arrays are [K][J][NXP], rows = J * K)
     bool grid_set = false;
-    int I = 0, J = 0, NXP = 0;
-    double lo[2] = {0, 0}, hi[2] = {1, 1};
+    int dim = 2;
+    int I = 0, J = 0, K = 1, NXP = 0;
+    long long rows = 0;
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
     bool homog = false;
     float sigma_t_homog = 1.f;
     DevBuf sigt, sigs, q;
 
     // inflow (host copies; uploaded at solve time)
-    std::vector<double> inflow_iso[4];
-    std::vector<double> inflow_ord[4];
+    std::vector<double> inflow_iso[6];
+    std::vector<double> inflow_ord[6];
     bool inflow_dirty = true;
     DevBuf inflow_dev;
     bool inflow_any = false;
@@ -72,8 +75,9 @@ struct rom_ctx {
     long long Mtot = 0;
     std::vector<int> M;            // per sample
     std::vector<long long> off;    // first ordinate per sample
-    std::vector<unsigned char> quad;  // explicit sets: quadrant code per ordinate
-    DevBuf c64, s64, z64, w64, c32, s32, w32;
+    std::vector<unsigned char> quad;  // explicit sets: octant code per ordinate (bits c<0, s<0, z<0)
+    bool seed_octants = false;        // seeded sets: 3D (8 m points) or X-Y (4 m)
+    DevBuf c64, s64, z64, w64, c32, s32, z32, w32;
 
     // kernel
     int kernel_kind = ROM_KERNEL_ISO;
@@ -87,6 +91,10 @@ struct rom_ctx {
     std::vector<SweepItem> items;
     std::vector<int> item_begin;
     DevBuf items_dev, item_begin_dev;
+    // 3D: CTA item lists (one octant each) and the tile hand-off buffers
+    std::vector<int> cta_begin, cta_list;
+    DevBuf cta_begin_dev, cta_list_dev, xface, yface, err3;
+    int n_ctas3 = 0, nwarps3 = 1, n_tx = 1, n_ty = 1;
 
     // dense scattering operator (mode 0)
     DevBuf psi, src_ord, Amat, dtab;
@@ -172,47 +180,61 @@ void reset_ordinate_dependents(rom_ctx *ctx)
 {
     ctx->pmat_dirty = true;
     ctx->tuned_g = 0;
-    for (int f = 0; f < 4; ++f) ctx->inflow_ord[f].clear();
+    for (int f = 0; f < 6; ++f) ctx->inflow_ord[f].clear();
     ctx->inflow_dirty = true;
     ctx->items_dirty = true;
     ctx->solved = false;
     invalidate_graph(ctx);
 }
 
-int face_cells(const rom_ctx *ctx, int face) { return face < 2 ? ctx->J : ctx->I; }
+int n_faces(const rom_ctx *ctx) { return ctx->dim == 3 ? 6 : 4; }
 
-int face_offset(const rom_ctx *ctx, int face)
+// cells of a face: 2D x faces J, y faces I; 3D x faces K*J, y faces K*I, z faces J*I
+long long face_cells(const rom_ctx *ctx, int face)
 {
-    switch (face) {
-    case 0: return 0;
-    case 1: return ctx->J;
-    case 2: return 2 * ctx->J;
-    default: return 2 * ctx->J + ctx->I;
-    }
+    const long long K = ctx->dim == 3 ? ctx->K : 1;
+    if (face < 2) return K * ctx->J;
+    if (face < 4) return K * ctx->I;
+    return (long long)ctx->J * ctx->I;
 }
+
+long long face_offset(const rom_ctx *ctx, int face)
+{
+    long long o = 0;
+    for (int f = 0; f < face; ++f) o += face_cells(ctx, f);
+    return o;
+}
+
+long long n_cells(const rom_ctx *ctx) { return (long long)ctx->I * ctx->J * ctx->K; }
+long long padded_cells(const rom_ctx *ctx) { return ctx->rows * ctx->NXP; }
 
 int set_grid_common(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3],
                     const double hi[3])
 {
-    if (dim == 3) return fail(ctx, ROM_ERR_UNSUPPORTED, "dim = 3 is not built");
-    if (dim != 2) return fail(ctx, ROM_ERR_INVALID_ARG, "dim must be 2 (got %d)", dim);
+    if (dim != 2 && dim != 3) return fail(ctx, ROM_ERR_INVALID_ARG, "dim must be 2 or 3 (got %d)", dim);
     if (!n || !lo || !hi) return fail(ctx, ROM_ERR_INVALID_ARG, "n, lo, hi must not be NULL");
-    if (n[0] < 1 || n[1] < 1) return fail(ctx, ROM_ERR_INVALID_ARG, "grid sizes must be >= 1");
-    if (n[0] > 32 * romk::kMaxWarps * romk::kCols)
+    if (n[0] < 1 || n[1] < 1 || (dim == 3 && n[2] < 1))
+        return fail(ctx, ROM_ERR_INVALID_ARG, "grid sizes must be >= 1");
+    if (dim == 2 && n[0] > 32 * romk::kMaxWarps * romk::kCols)
         return fail(ctx, ROM_ERR_INVALID_ARG, "I = %lld exceeds %d", (long long)n[0],
                     32 * romk::kMaxWarps * romk::kCols);
+    if (dim == 3 && (n[0] > 4096 || n[1] > 4096 || n[2] > 4096))
+        return fail(ctx, ROM_ERR_INVALID_ARG, "3D grid sizes are limited to 4096 per axis");
     if (n[1] > (1 << 24)) return fail(ctx, ROM_ERR_INVALID_ARG, "J too large");
-    if (!(hi[0] > lo[0]) || !(hi[1] > lo[1]) || !isfinite(lo[0]) || !isfinite(hi[0]) ||
-        !isfinite(lo[1]) || !isfinite(hi[1]))
-        return fail(ctx, ROM_ERR_INVALID_ARG, "need hi > lo (finite)");
+    for (int d = 0; d < dim; ++d)
+        if (!(hi[d] > lo[d]) || !isfinite(lo[d]) || !isfinite(hi[d]))
+            return fail(ctx, ROM_ERR_INVALID_ARG, "need hi > lo (finite)");
+    ctx->dim = dim;
     ctx->I = (int)n[0];
     ctx->J = (int)n[1];
+    ctx->K = dim == 3 ? (int)n[2] : 1;
+    ctx->rows = (long long)ctx->J * ctx->K;
     ctx->NXP = (ctx->I + romk::kCols - 1) / romk::kCols * romk::kCols;
-    ctx->lo[0] = lo[0];
-    ctx->lo[1] = lo[1];
-    ctx->hi[0] = hi[0];
-    ctx->hi[1] = hi[1];
-    for (int f = 0; f < 4; ++f) {
+    for (int d = 0; d < 3; ++d) {
+        ctx->lo[d] = d < dim ? lo[d] : 0.0;
+        ctx->hi[d] = d < dim ? hi[d] : 1.0;
+    }
+    for (int f = 0; f < 6; ++f) {
         ctx->inflow_iso[f].clear();
         ctx->inflow_ord[f].clear();
     }
@@ -221,7 +243,7 @@ int set_grid_common(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3
     ctx->tuned_g = 0;
     ctx->solved = false;
     invalidate_graph(ctx);
-    const size_t bytes = (size_t)ctx->J * ctx->NXP * sizeof(float);
+    const size_t bytes = (size_t)padded_cells(ctx) * sizeof(float);
     int rc;
     if ((rc = ensure(ctx, ctx->sigt, bytes)) || (rc = ensure(ctx, ctx->sigs, bytes)) ||
         (rc = ensure(ctx, ctx->q, bytes)))
@@ -240,6 +262,7 @@ int source_mode(const rom_ctx *ctx)
 
 int choose_g(const rom_ctx *ctx)
 {
+    if (ctx->dim == 3) return ctx->opt.tile_g == 1 ? 1 : 2;
     const int cap = source_mode(ctx) == 0 ? 2 : 4;  // dense mode: registers for 2 ordinates
     if (ctx->opt.tile_g == 1 || ctx->opt.tile_g == 2 || ctx->opt.tile_g == 4)
         return std::min(ctx->opt.tile_g, cap);
@@ -254,8 +277,99 @@ int choose_g(const rom_ctx *ctx)
     return 1;
 }
 
+// 3D: work items of G = 2 ordinates of one sample and octant (1 with tile_g =
+// 1); CTAs take strided lists of the items of one octant (consecutive CTAs of
+// an octant work on neighbouring items, hence on the same few samples at a
+// time); CTAs per octant in proportion to its items.
+int build_items3(rom_ctx *ctx)
+{
+    const int G = ctx->opt.tile_g == 1 ? 1 : 2;
+    ctx->G_used = G;
+    ctx->items.clear();
+    ctx->item_begin.resize(ctx->S + 1);
+    std::vector<int> byo[8];
+    for (int s = 0; s < ctx->S; ++s) {
+        ctx->item_begin[s] = s;  // the combine reads one accumulated array per sample
+        std::vector<int> ords[8];
+        for (int l = 0; l < ctx->M[s]; ++l) {
+            const long long o = ctx->off[s] + l;
+            int code;
+            if (ctx->ord_source == ORD_SEED) {
+                // generated blocks of m: (+,+), (-,+), (-,-), (+,-), then (3D) the same with zeta < 0
+                const int m = ctx->M[s] / (ctx->seed_octants ? 8 : 4);
+                const int qd = l / m;
+                const int q4 = qd & 3;
+                code = (q4 == 0 ? 0 : q4 == 1 ? 1 : q4 == 2 ? 3 : 2) | (qd >= 4 ? 4 : 0);
+            } else {
+                code = ctx->quad[o];
+            }
+            ords[code].push_back((int)o);
+        }
+        for (int code = 0; code < 8; ++code)
+            for (size_t k = 0; k < ords[code].size(); k += G) {
+                SweepItem it{};
+                it.sample = s;
+                it.quad = code;
+                it.n = (int)std::min<size_t>(G, ords[code].size() - k);
+                for (int t = 0; t < romk::kMaxG; ++t)
+                    it.ord[t] = ords[code][k + (t < it.n ? t : 0)];
+                byo[code].push_back((int)ctx->items.size());
+                ctx->items.push_back(it);
+            }
+    }
+    ctx->item_begin[ctx->S] = ctx->S;
+    const long long total = (long long)ctx->items.size();
+    const int L = (ctx->I + romk::kCols - 1) / romk::kCols;
+    const int strips = romk::sweep3d_tile_cols() / romk::kCols;
+    ctx->nwarps3 = std::min(strips, L);
+    ctx->n_tx = (L + strips - 1) / strips;
+    ctx->n_ty = (ctx->J + 127) / 128;
+    const int grid = ctx->sm_count * romk::sweep3d_ctas_per_sm(ctx->nwarps3, G);
+    ctx->cta_begin.assign(1, 0);
+    ctx->cta_list.clear();
+    for (int code = 0; code < 8; ++code) {
+        const std::vector<int> &v = byo[code];
+        if (v.empty()) continue;
+        long long P = std::max<long long>(1, (long long)llround((double)grid * v.size() / total));
+        P = std::min<long long>(P, (long long)v.size());
+        P = std::max<long long>(P, ((long long)v.size() + romk::kMaxCtaItems3 - 1) / romk::kMaxCtaItems3);
+        for (long long b = 0; b < P; ++b) {
+            for (long long k = b; k < (long long)v.size(); k += P) ctx->cta_list.push_back(v[k]);
+            ctx->cta_begin.push_back((int)ctx->cta_list.size());
+        }
+    }
+    ctx->n_ctas3 = (int)ctx->cta_begin.size() - 1;
+    int rc;
+    if ((rc = ensure(ctx, ctx->items_dev, ctx->items.size() * sizeof(SweepItem))) ||
+        (rc = ensure(ctx, ctx->item_begin_dev, ctx->item_begin.size() * sizeof(int))) ||
+        (rc = ensure(ctx, ctx->cta_begin_dev, ctx->cta_begin.size() * sizeof(int))) ||
+        (rc = ensure(ctx, ctx->cta_list_dev, ctx->cta_list.size() * sizeof(int))) ||
+        (rc = ensure(ctx, ctx->err3, sizeof(int))))
+        return rc;
+    if (ctx->n_tx > 1 &&
+        (rc = ensure(ctx, ctx->xface, (size_t)total * G * ctx->K * ctx->J * sizeof(float))))
+        return rc;
+    if (ctx->n_ty > 1 &&
+        (rc = ensure(ctx, ctx->yface, (size_t)total * G * ctx->K * ctx->NXP * sizeof(float))))
+        return rc;
+    if (!ctx->items.empty())
+        CK(cudaMemcpyAsync(ctx->items_dev.p, ctx->items.data(), ctx->items.size() * sizeof(SweepItem),
+                           cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->item_begin_dev.p, ctx->item_begin.data(),
+                       ctx->item_begin.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->cta_begin_dev.p, ctx->cta_begin.data(),
+                       ctx->cta_begin.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    if (!ctx->cta_list.empty())
+        CK(cudaMemcpyAsync(ctx->cta_list_dev.p, ctx->cta_list.data(),
+                           ctx->cta_list.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->items_dirty = false;
+    return ROM_OK;
+}
+
 int build_items(rom_ctx *ctx)
 {
+    if (ctx->dim == 3) return build_items3(ctx);
     const int G = choose_g(ctx);
     ctx->G_used = G;
     ctx->items.clear();
@@ -265,17 +379,20 @@ int build_items(rom_ctx *ctx)
         ctx->item_begin[s] = (int)ctx->items.size();
         for (int qd = 0; qd < 4; ++qd) byq[qd].clear();
         if (ctx->ord_source == ORD_SEED) {
-            const int m = ctx->M[s] / 4;
-            for (int qd = 0; qd < 4; ++qd)
+            const int nblk = ctx->seed_octants ? 8 : 4;
+            const int m = ctx->M[s] / nblk;
+            for (int qd = 0; qd < nblk; ++qd)
                 for (int l = 0; l < m; ++l) {
                     // quadrant blocks of the generated set: (+,+), (-,+), (-,-), (+,-)
-                    const int code = qd == 0 ? 0 : qd == 1 ? 1 : qd == 2 ? 3 : 2;
+                    // (3D sets repeat them with zeta < 0; X-Y sweeps ignore zeta)
+                    const int q4 = qd & 3;
+                    const int code = q4 == 0 ? 0 : q4 == 1 ? 1 : q4 == 2 ? 3 : 2;
                     byq[code].push_back((int)(ctx->off[s] + (long long)qd * m + l));
                 }
         } else {
             for (int l = 0; l < ctx->M[s]; ++l) {
                 const long long o = ctx->off[s] + l;
-                byq[ctx->quad[o]].push_back((int)o);
+                byq[ctx->quad[o] & 3].push_back((int)o);
             }
         }
         for (int code = 0; code < 4; ++code) {
@@ -308,11 +425,12 @@ int build_items(rom_ctx *ctx)
 int upload_inflow(rom_ctx *ctx)
 {
     bool any_ord = false, any_iso = false;
-    for (int f = 0; f < 4; ++f) {
+    const int NF = n_faces(ctx);
+    for (int f = 0; f < NF; ++f) {
         any_ord |= !ctx->inflow_ord[f].empty();
         any_iso |= !ctx->inflow_iso[f].empty();
     }
-    const long long nface = 2LL * ctx->I + 2LL * ctx->J;
+    const long long nface = face_offset(ctx, NF);
     ctx->inflow_any = any_ord || any_iso;
     if (!ctx->inflow_any) {
         ctx->inflow_dirty = false;
@@ -322,9 +440,9 @@ int upload_inflow(rom_ctx *ctx)
     ctx->inflow_stride = any_ord ? nface : 0;
     std::vector<float> h((size_t)(rows * nface), 0.f);
     for (long long o = 0; o < rows; ++o)
-        for (int f = 0; f < 4; ++f) {
-            const int nf = face_cells(ctx, f), fo = face_offset(ctx, f);
-            for (int k = 0; k < nf; ++k) {
+        for (int f = 0; f < NF; ++f) {
+            const long long nf = face_cells(ctx, f), fo = face_offset(ctx, f);
+            for (long long k = 0; k < nf; ++k) {
                 double v = 0.0;
                 if (!ctx->inflow_ord[f].empty()) v = ctx->inflow_ord[f][(size_t)o * nf + k];
                 else if (!ctx->inflow_iso[f].empty()) v = ctx->inflow_iso[f][k];
@@ -364,6 +482,38 @@ romk::SweepArgs sweep_args(const rom_ctx *ctx)
         a.src = (const float *)ctx->src_ord.p;
         a.psi = (float *)ctx->psi.p;
     }
+    return a;
+}
+
+romk::Sweep3Args sweep3_args(const rom_ctx *ctx)
+{
+    romk::Sweep3Args a{};
+    a.I = ctx->I;
+    a.J = ctx->J;
+    a.K = ctx->K;
+    a.NXP = ctx->NXP;
+    a.inv_dx = (float)(ctx->I / (ctx->hi[0] - ctx->lo[0]));
+    a.inv_dy = (float)(ctx->J / (ctx->hi[1] - ctx->lo[1]));
+    a.inv_dz = (float)(ctx->K / (ctx->hi[2] - ctx->lo[2]));
+    a.sigma_t = (const float *)ctx->sigt.p;
+    a.src = (const float *)ctx->src.p;
+    a.phi = (float *)ctx->part.p;
+    a.items = (const SweepItem *)ctx->items_dev.p;
+    a.cta_begin = (const int *)ctx->cta_begin_dev.p;
+    a.cta_list = (const int *)ctx->cta_list_dev.p;
+    a.oc = (const float *)ctx->c32.p;
+    a.os = (const float *)ctx->s32.p;
+    a.oz = (const float *)ctx->z32.p;
+    a.ow = (const float *)ctx->w32.p;
+    a.inflow = ctx->inflow_any ? (const float *)ctx->inflow_dev.p : nullptr;
+    a.inflow_stride = ctx->inflow_stride;
+    a.active = (const int *)ctx->active.p;
+    a.cells = padded_cells(ctx);
+    a.n_tx = ctx->n_tx;
+    a.n_ty = ctx->n_ty;
+    a.xface = (float *)ctx->xface.p;
+    a.yface = (float *)ctx->yface.p;
+    a.err = (int *)ctx->err3.p;
     return a;
 }
 
@@ -454,23 +604,41 @@ int prepare_dense(rom_ctx *ctx)
     return ROM_OK;
 }
 
-// One source-iteration sweep: K1 + K2 (+ K4 in dense mode) + K5.
+int launches_per_iteration(const rom_ctx *ctx)
+{
+    if (ctx->dim == 3) return ctx->n_tx * ctx->n_ty + 2;
+    return ctx->MOM == 0 ? 4 : 3;
+}
+
+// One source-iteration sweep: K1 (K9 per tile in 3D) + K2 (+ K4 in dense mode) + K5.
 int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphConditionalHandle h,
                       cudaEvent_t k0 = nullptr, cudaEvent_t k1 = nullptr,
                       cudaEvent_t k2 = nullptr, cudaEvent_t k3 = nullptr)
 {
-    const romk::SweepArgs sa = sweep_args(ctx);
-    const int L = (ctx->I + romk::kCols - 1) / romk::kCols;
-    const int nwarps = (L + 31) / 32;
     if (k0) CK(cudaEventRecord(k0, st));
-    CK(romk::launch_sweep2d(sa, (int)ctx->items.size(), nwarps, ctx->G_used, ctx->opt.scheme,
-                            ctx->homog, ctx->MOM, st));
+    if (ctx->dim == 3) {
+        romk::Sweep3Args a3 = sweep3_args(ctx);
+        for (int ty = 0; ty < ctx->n_ty; ++ty)
+            for (int tx = 0; tx < ctx->n_tx; ++tx) {
+                a3.tile_x = tx;
+                a3.tile_y = ty;
+                CK(romk::launch_sweep3d(a3, ctx->n_ctas3, ctx->nwarps3, ctx->G_used,
+                                        ctx->opt.scheme, st));
+            }
+    } else {
+        const romk::SweepArgs sa = sweep_args(ctx);
+        const int L = (ctx->I + romk::kCols - 1) / romk::kCols;
+        const int nwarps = (L + 31) / 32;
+        CK(romk::launch_sweep2d(sa, (int)ctx->items.size(), nwarps, ctx->G_used, ctx->opt.scheme,
+                                ctx->homog, ctx->MOM, st));
+    }
     if (k1) CK(cudaEventRecord(k1, st));
     romk::CombineArgs ca{};
     ca.S = ctx->S;
     ca.MOM = ctx->MOM == 0 ? 1 : ctx->MOM;
+    ca.zero_part = ctx->dim == 3 ? 1 : 0;
     ca.chunks = ctx->chunks;
-    ca.cells = (long long)ctx->J * ctx->NXP;
+    ca.cells = padded_cells(ctx);
     ca.cells4 = ca.cells / 4;
     ca.g = (float)ctx->g;
     ca.part = (const float *)ctx->part.p;
@@ -645,7 +813,8 @@ void rom_destroy(rom_ctx *ctx)
                       &ctx->item_begin_dev, &ctx->phi, &ctx->src, &ctx->part, &ctx->partials,
                       &ctx->active, &ctx->iters, &ctx->flags, &ctx->resid, &ctx->n_active,
                       &ctx->avg, &ctx->sum, &ctx->tmp, &ctx->psi, &ctx->src_ord, &ctx->Amat,
-                      &ctx->dtab};
+                      &ctx->dtab, &ctx->z32, &ctx->cta_begin_dev, &ctx->cta_list_dev,
+                      &ctx->xface, &ctx->yface, &ctx->err3};
     for (DevBuf *b : bufs) release(*b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -697,8 +866,9 @@ int rom_set_grid(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3], 
     if (!sigma_t || !sigma_s || !q) return fail(ctx, ROM_ERR_INVALID_ARG, "NULL coefficient array");
     CK(cudaSetDevice(ctx->device));
     ctx->grid_set = false;
-    if (dim == 2 && n && n[0] >= 1 && n[1] >= 1) {
-        const size_t nc = (size_t)n[0] * (size_t)n[1];
+    if ((dim == 2 || dim == 3) && n && n[0] >= 1 && n[1] >= 1 && (dim == 2 || n[2] >= 1) &&
+        n[0] <= 4096 && n[1] <= 4096 && (dim == 2 || n[2] <= 4096)) {
+        const size_t nc = (size_t)n[0] * (size_t)n[1] * (size_t)(dim == 3 ? n[2] : 1);
         for (size_t k = 0; k < nc; ++k) {
             const double a = sigma_t[k], b = sigma_s[k], c = q[k];
             if (!(isfinite(a) && isfinite(b) && isfinite(c) && b >= 0.0 && b < a && c >= 0.0))
@@ -709,10 +879,11 @@ int rom_set_grid(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3], 
     }
     int rc = set_grid_common(ctx, dim, n, lo, hi);
     if (rc) return rc;
-    const int I = ctx->I, J = ctx->J, NXP = ctx->NXP;
+    const int I = ctx->I, NXP = ctx->NXP;
+    const long long J = ctx->rows;  // 3D: the K * J rows of [K][J][I]
     std::vector<float> hs((size_t)J * NXP), hss((size_t)J * NXP), hq((size_t)J * NXP);
     double mn = sigma_t[0], mx = sigma_t[0];
-    for (int j = 0; j < J; ++j)
+    for (long long j = 0; j < J; ++j)
         for (int i = 0; i < NXP; ++i) {
             const size_t d = (size_t)j * NXP + i;
             if (i < I) {
@@ -752,7 +923,7 @@ int rom_set_grid_device(rom_ctx *ctx, int dim, const int64_t n[3], const double 
     if ((rc = ensure(ctx, ctx->tmp, 4 * sizeof(unsigned int)))) return rc;
     unsigned int init[3] = {0x7f800000u, 0u, 0u};  // +inf bits, 0, 0
     CK(cudaMemcpyAsync(ctx->tmp.p, init, sizeof init, cudaMemcpyHostToDevice, ctx->stream));
-    CK(romk::launch_pad_grid(sigma_t, sigma_s, q, ctx->I, ctx->J, ctx->NXP, (float *)ctx->sigt.p,
+    CK(romk::launch_pad_grid(sigma_t, sigma_s, q, ctx->I, (int)ctx->rows, ctx->NXP, (float *)ctx->sigt.p,
                              (float *)ctx->sigs.p, (float *)ctx->q.p, (unsigned int *)ctx->tmp.p,
                              ctx->stream));
     ++ctx->launches;
@@ -775,12 +946,13 @@ int rom_set_inflow_isotropic(rom_ctx *ctx, int face, const double *psi_face)
 {
     if (!ctx) return ROM_ERR_INVALID_ARG;
     if (!ctx->grid_set) return fail(ctx, ROM_ERR_STATE, "set the grid first");
-    if (face < 0 || face > 3) return fail(ctx, ROM_ERR_INVALID_ARG, "face must be 0..3");
+    if (face < 0 || face >= n_faces(ctx))
+        return fail(ctx, ROM_ERR_INVALID_ARG, "face must be 0..%d", n_faces(ctx) - 1);
     ctx->inflow_iso[face].clear();
     ctx->inflow_ord[face].clear();
     if (psi_face) {
-        const int nf = face_cells(ctx, face);
-        for (int k = 0; k < nf; ++k)
+        const long long nf = face_cells(ctx, face);
+        for (long long k = 0; k < nf; ++k)
             if (!(psi_face[k] >= 0.0) || !isfinite(psi_face[k]))
                 return fail(ctx, ROM_ERR_INVALID_ARG, "inflow must be finite and >= 0");
         ctx->inflow_iso[face].assign(psi_face, psi_face + nf);
@@ -795,7 +967,8 @@ int rom_set_inflow_ordinates(rom_ctx *ctx, int face, const double *psi)
     if (!ctx) return ROM_ERR_INVALID_ARG;
     if (!ctx->grid_set) return fail(ctx, ROM_ERR_STATE, "set the grid first");
     if (ctx->ord_source == ORD_NONE) return fail(ctx, ROM_ERR_STATE, "set the ordinates first");
-    if (face < 0 || face > 3) return fail(ctx, ROM_ERR_INVALID_ARG, "face must be 0..3");
+    if (face < 0 || face >= n_faces(ctx))
+        return fail(ctx, ROM_ERR_INVALID_ARG, "face must be 0..%d", n_faces(ctx) - 1);
     ctx->inflow_iso[face].clear();
     ctx->inflow_ord[face].clear();
     if (psi) {
@@ -843,7 +1016,7 @@ int rom_set_ordinates(rom_ctx *ctx, int n_samples, const int32_t *m_per_sample,
     }
     ctx->quad.resize(tot);
     std::vector<double> c(tot), s(tot), z(tot), w(tot);
-    std::vector<float> cf(tot), sf(tot), wf(tot);
+    std::vector<float> cf(tot), sf(tot), zf(tot), wf(tot);
     for (long long o = 0; o < tot; ++o) {
         c[o] = dirs[3 * o];
         s[o] = dirs[3 * o + 1];
@@ -851,15 +1024,17 @@ int rom_set_ordinates(rom_ctx *ctx, int n_samples, const int32_t *m_per_sample,
         w[o] = weights[o];
         cf[o] = (float)c[o];
         sf[o] = (float)s[o];
+        zf[o] = (float)z[o];
         wf[o] = (float)w[o];
-        ctx->quad[o] = (unsigned char)((c[o] < 0.0 ? 1 : 0) | (s[o] < 0.0 ? 2 : 0));
+        ctx->quad[o] =
+            (unsigned char)((c[o] < 0.0 ? 1 : 0) | (s[o] < 0.0 ? 2 : 0) | (z[o] < 0.0 ? 4 : 0));
     }
     int rc;
     const size_t b8 = tot * sizeof(double), b4 = tot * sizeof(float);
     if ((rc = ensure(ctx, ctx->c64, b8)) || (rc = ensure(ctx, ctx->s64, b8)) ||
         (rc = ensure(ctx, ctx->z64, b8)) || (rc = ensure(ctx, ctx->w64, b8)) ||
         (rc = ensure(ctx, ctx->c32, b4)) || (rc = ensure(ctx, ctx->s32, b4)) ||
-        (rc = ensure(ctx, ctx->w32, b4)))
+        (rc = ensure(ctx, ctx->z32, b4)) || (rc = ensure(ctx, ctx->w32, b4)))
         return rc;
     CK(cudaMemcpyAsync(ctx->c64.p, c.data(), b8, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->s64.p, s.data(), b8, cudaMemcpyHostToDevice, ctx->stream));
@@ -867,15 +1042,21 @@ int rom_set_ordinates(rom_ctx *ctx, int n_samples, const int32_t *m_per_sample,
     CK(cudaMemcpyAsync(ctx->w64.p, w.data(), b8, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->c32.p, cf.data(), b4, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->s32.p, sf.data(), b4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->z32.p, zf.data(), b4, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->w32.p, wf.data(), b4, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->ord_source = ORD_EXPLICIT;
+    ctx->seed_octants = false;
     reset_ordinate_dependents(ctx);
     return ROM_OK;
 }
 
-int rom_set_ordinates_seed_offset(rom_ctx *ctx, uint64_t seed, int first_sample, int n_samples,
-                                  const int32_t *n_zeta, const int32_t *n_theta)
+}  // extern "C"
+
+namespace {
+
+int set_ordinates_seeded(rom_ctx *ctx, uint64_t seed, int first_sample, int n_samples,
+                         const int32_t *n_zeta, const int32_t *n_theta, bool octants)
 {
     if (!ctx) return ROM_ERR_INVALID_ARG;
     if (n_samples < 1 || first_sample < 0 || !n_zeta || !n_theta)
@@ -883,7 +1064,9 @@ int rom_set_ordinates_seed_offset(rom_ctx *ctx, uint64_t seed, int first_sample,
     if ((long long)first_sample + n_samples > (1LL << 31))
         return fail(ctx, ROM_ERR_INVALID_ARG, "sample index out of range");
     CK(cudaSetDevice(ctx->device));
-    const bool same_layout = ctx->ord_source == ORD_SEED && ctx->S == n_samples;
+    const bool same_layout =
+        ctx->ord_source == ORD_SEED && ctx->S == n_samples && ctx->seed_octants == octants;
+    const int per_cell = octants ? 8 : 4;
     std::vector<int> nz(n_zeta, n_zeta + n_samples), nt(n_theta, n_theta + n_samples);
     std::vector<int> first_cell(n_samples + 1, 0);
     std::vector<long long> off(n_samples);
@@ -896,8 +1079,8 @@ int rom_set_ordinates_seed_offset(rom_ctx *ctx, uint64_t seed, int first_sample,
         const int m = nz[s] * nt[s];
         first_cell[s + 1] = first_cell[s] + m;
         off[s] = tot;
-        M[s] = 4 * m;
-        tot += 4LL * m;
+        M[s] = per_cell * m;
+        tot += (long long)per_cell * m;
         if (first_cell[s + 1] > (1 << 30)) return fail(ctx, ROM_ERR_INVALID_ARG, "too many cells");
     }
     bool layout_same = same_layout && ctx->M == M;
@@ -910,7 +1093,7 @@ int rom_set_ordinates_seed_offset(rom_ctx *ctx, uint64_t seed, int first_sample,
     if ((rc = ensure(ctx, ctx->c64, b8)) || (rc = ensure(ctx, ctx->s64, b8)) ||
         (rc = ensure(ctx, ctx->z64, b8)) || (rc = ensure(ctx, ctx->w64, b8)) ||
         (rc = ensure(ctx, ctx->c32, b4)) || (rc = ensure(ctx, ctx->s32, b4)) ||
-        (rc = ensure(ctx, ctx->w32, b4)))
+        (rc = ensure(ctx, ctx->z32, b4)) || (rc = ensure(ctx, ctx->w32, b4)))
         return rc;
     // small per-sample tables packed into one device buffer
     const size_t tb = (size_t)n_samples * (2 * sizeof(int) + sizeof(long long)) +
@@ -940,25 +1123,44 @@ int rom_set_ordinates_seed_offset(rom_ctx *ctx, uint64_t seed, int first_sample,
     a.ord_off = (const long long *)(base + o_off);
     a.first_sample = first_sample;
     a.total_cells = first_cell[n_samples];
+    a.octants = octants ? 1 : 0;
     a.c64 = (double *)ctx->c64.p;
     a.s64 = (double *)ctx->s64.p;
     a.z64 = (double *)ctx->z64.p;
     a.w64 = (double *)ctx->w64.p;
     a.c32 = (float *)ctx->c32.p;
     a.s32 = (float *)ctx->s32.p;
+    a.z32 = (float *)ctx->z32.p;
     a.w32 = (float *)ctx->w32.p;
     CK(romk::launch_ordgen(a, ctx->stream));
     ++ctx->launches;
     CK(cudaStreamSynchronize(ctx->stream));  // the packed host table dies with this call
     ctx->ord_source = ORD_SEED;
+    ctx->seed_octants = octants;
     if (layout_same) {
         // same sample layout: work items, buffers and the captured graph stay valid
-        for (int f = 0; f < 4; ++f) ctx->inflow_ord[f].clear();
+        for (int f = 0; f < 6; ++f) ctx->inflow_ord[f].clear();
         ctx->solved = false;
     } else {
         reset_ordinate_dependents(ctx);
     }
     return ROM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rom_set_ordinates_seed_offset(rom_ctx *ctx, uint64_t seed, int first_sample, int n_samples,
+                                  const int32_t *n_zeta, const int32_t *n_theta)
+{
+    return set_ordinates_seeded(ctx, seed, first_sample, n_samples, n_zeta, n_theta, false);
+}
+
+int rom_set_ordinates_seed_xyz(rom_ctx *ctx, uint64_t seed, int first_sample, int n_samples,
+                               const int32_t *n_zeta, const int32_t *n_theta)
+{
+    return set_ordinates_seeded(ctx, seed, first_sample, n_samples, n_zeta, n_theta, true);
 }
 
 int rom_set_ordinates_seed(rom_ctx *ctx, uint64_t seed, int n_samples, const int32_t *n_zeta,
@@ -1048,8 +1250,11 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     if (ctx->ord_source == ORD_NONE) return fail(ctx, ROM_ERR_STATE, "set the ordinates first");
     CK(cudaSetDevice(ctx->device));
     int rc;
-    const long long cells = (long long)ctx->J * ctx->NXP;
+    const long long cells = padded_cells(ctx);
     const int mode = source_mode(ctx);
+    if (ctx->dim == 3 && mode != 1)
+        return fail(ctx, ROM_ERR_UNSUPPORTED,
+                    "3D grids support the isotropic kernel with angular moments only");
     if (mode != ctx->MOM) {
         ctx->MOM = mode;
         ctx->items_dirty = true;
@@ -1069,10 +1274,12 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     ctx->chunks = chunks;
     const int MOM = ctx->MOM == 0 ? 1 : ctx->MOM;  // moments kept per sample
     const size_t state = (size_t)ctx->S * MOM * cells * sizeof(float);
-    const size_t nI = (size_t)ctx->I * ctx->J;
+    const size_t nI = (size_t)n_cells(ctx);
+    // part: per work item (2D), or the accumulated flux of each sample (3D)
+    const size_t part_units = ctx->dim == 3 ? (size_t)ctx->S : ctx->items.size();
     void *before[] = {ctx->phi.p, ctx->src.p, ctx->part.p, ctx->partials.p, ctx->active.p};
     if ((rc = ensure(ctx, ctx->phi, state)) || (rc = ensure(ctx, ctx->src, state)) ||
-        (rc = ensure(ctx, ctx->part, ctx->items.size() * MOM * cells * sizeof(float))) ||
+        (rc = ensure(ctx, ctx->part, part_units * MOM * cells * sizeof(float))) ||
         (rc = ensure(ctx, ctx->partials, (size_t)ctx->S * chunks * 2 * sizeof(double))) ||
         (rc = ensure(ctx, ctx->active, ctx->S * sizeof(int))) ||
         (rc = ensure(ctx, ctx->iters, ctx->S * sizeof(int))) ||
@@ -1088,7 +1295,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
         void *dense_after[] = {ctx->psi.p, ctx->src_ord.p, ctx->Amat.p, ctx->dtab.p};
         if (memcmp(dense_before, dense_after, sizeof dense_before) != 0) invalidate_graph(ctx);
     }
-    if (ctx->opt.tile_g == -1 && ctx->tuned_g == 0) {
+    if (ctx->dim == 2 && ctx->opt.tile_g == -1 && ctx->tuned_g == 0) {
         if ((rc = autotune_g(ctx))) return rc;
         if ((rc = build_items(ctx))) return rc;
         if ((rc = ensure(ctx, ctx->part, ctx->items.size() * MOM * cells * sizeof(float))))
@@ -1100,6 +1307,10 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
 
     const long long launches0 = ctx->launches;
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    if (ctx->dim == 3) {  // the sweep accumulates into part; the combine clears it
+        CK(cudaMemsetAsync(ctx->part.p, 0, part_units * cells * sizeof(float), ctx->stream));
+        CK(cudaMemsetAsync(ctx->err3.p, 0, sizeof(int), ctx->stream));
+    }
     CK(romk::launch_init_state(ctx->S, MOM, cells, (const float *)ctx->q.p, (float *)ctx->phi.p,
                                (float *)ctx->src.p, (int *)ctx->active.p, (int *)ctx->iters.p,
                                (int *)ctx->flags.p, (double *)ctx->resid.p, ctx->stream));
@@ -1135,7 +1346,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
                 cudaEvent_t k2 = timed && ctx->MOM == 0 ? ctx->kev[4 * k + 2] : nullptr;
                 cudaEvent_t k3 = timed && ctx->MOM == 0 ? ctx->kev[4 * k + 3] : nullptr;
                 if ((rc = enqueue_iteration(ctx, ctx->stream, false, 0, k0, k1, k2, k3))) return rc;
-                ctx->launches += ctx->MOM == 0 ? 4 : 3;
+                ctx->launches += launches_per_iteration(ctx);
             }
             done += n;
             int n_active = 0;
@@ -1157,13 +1368,16 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
             if (n_active == 0) break;
         }
     }
-    CK(romk::launch_average((const float *)ctx->phi.p, ctx->S, MOM, ctx->I, ctx->J, ctx->NXP,
-                            (double *)ctx->avg.p, (double *)ctx->sum.p, ctx->stream));
+    CK(romk::launch_average((const float *)ctx->phi.p, ctx->S, MOM, ctx->I, (int)ctx->rows,
+                            ctx->NXP, (double *)ctx->avg.p, (double *)ctx->sum.p, ctx->stream));
     ++ctx->launches;
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     ctx->h_iters.assign(ctx->S, 0);
     ctx->h_resid.assign(ctx->S, 0.0);
     std::vector<int> flags(ctx->S, 0);
+    int err3 = 0;
+    if (ctx->dim == 3)
+        CK(cudaMemcpyAsync(&err3, ctx->err3.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_iters.data(), ctx->iters.p, ctx->S * sizeof(int),
                        cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_resid.data(), ctx->resid.p, ctx->S * sizeof(double),
@@ -1173,6 +1387,8 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     CK(cudaStreamSynchronize(ctx->stream));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    if (err3)
+        return fail(ctx, ROM_ERR_CUDA, "3D sweep: a wait between warps timed out (flags %d)", err3);
     ctx->solved = true;
 
     rom_stats st{};
@@ -1184,7 +1400,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
         const int it = ctx->h_iters[s];
         st.iterations_max = std::max(st.iterations_max, it);
         st.iterations_min = std::min(st.iterations_min, it);
-        st.updates += (int64_t)ctx->I * ctx->J * ctx->M[s] * it;
+        st.updates += (int64_t)n_cells(ctx) * ctx->M[s] * it;
         const double r = ctx->h_resid[s];
         if (!(r <= st.residual_max)) st.residual_max = r;
         if (flags[s] & 1) ++diverged;
@@ -1196,7 +1412,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     st.source_ms = source_ms;
     st.source_launches = source_launches;
     st.tile_g = ctx->G_used;
-    if (device_loop) ctx->launches += (ctx->MOM == 0 ? 4LL : 3LL) * st.iterations_max;
+    if (device_loop) ctx->launches += (long long)launches_per_iteration(ctx) * st.iterations_max;
     st.kernel_launches = ctx->launches - launches0;
     if (stats_out) *stats_out = st;
     if (diverged) return fail(ctx, ROM_ERR_DIVERGED, "%d samples diverged (NaN/Inf residual)", diverged);
@@ -1212,13 +1428,13 @@ int rom_get_scalar_flux(rom_ctx *ctx, int sample, double *out)
     if (!ctx->solved) return fail(ctx, ROM_ERR_STATE, "call rom_solve first");
     if (sample < -1 || sample >= ctx->S) return fail(ctx, ROM_ERR_INVALID_ARG, "bad sample %d", sample);
     CK(cudaSetDevice(ctx->device));
-    const size_t nI = (size_t)ctx->I * ctx->J;
+    const size_t nI = (size_t)n_cells(ctx);
     if (sample >= 0) {
         int rc = ensure(ctx, ctx->tmp, nI * sizeof(double));
         if (rc) return rc;
         CK(romk::launch_extract((const float *)ctx->phi.p, sample, ctx->MOM == 0 ? 1 : ctx->MOM,
-                                ctx->I, ctx->J,
-                                ctx->NXP, (double *)ctx->tmp.p, ctx->stream));
+                                ctx->I, (int)ctx->rows, ctx->NXP, (double *)ctx->tmp.p,
+                                ctx->stream));
         ++ctx->launches;
         CK(cudaMemcpyAsync(out, ctx->tmp.p, nI * sizeof(double), cudaMemcpyDeviceToHost,
                            ctx->stream));
@@ -1236,11 +1452,10 @@ int rom_get_scalar_flux_device(rom_ctx *ctx, int sample, double *out)
     if (!ctx->solved) return fail(ctx, ROM_ERR_STATE, "call rom_solve first");
     if (sample < -1 || sample >= ctx->S) return fail(ctx, ROM_ERR_INVALID_ARG, "bad sample %d", sample);
     CK(cudaSetDevice(ctx->device));
-    const size_t nI = (size_t)ctx->I * ctx->J;
+    const size_t nI = (size_t)n_cells(ctx);
     if (sample >= 0) {
         CK(romk::launch_extract((const float *)ctx->phi.p, sample, ctx->MOM == 0 ? 1 : ctx->MOM,
-                                ctx->I, ctx->J,
-                                ctx->NXP, out, ctx->stream));
+                                ctx->I, (int)ctx->rows, ctx->NXP, out, ctx->stream));
         ++ctx->launches;
     } else {
         CK(cudaMemcpyAsync(out, ctx->avg.p, nI * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -1266,7 +1481,7 @@ int rom_get_partial_sum(rom_ctx *ctx, double *sum_out, int64_t *count_out)
     if (!ctx->solved) return fail(ctx, ROM_ERR_STATE, "call rom_solve first");
     CK(cudaSetDevice(ctx->device));
     if (sum_out) {
-        CK(cudaMemcpyAsync(sum_out, ctx->sum.p, (size_t)ctx->I * ctx->J * sizeof(double),
+        CK(cudaMemcpyAsync(sum_out, ctx->sum.p, (size_t)n_cells(ctx) * sizeof(double),
                            cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     }

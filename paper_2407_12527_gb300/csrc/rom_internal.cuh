@@ -10,6 +10,8 @@
 //   ordinates                c, s, w [M_total] (FP32) and c, s, zeta, w (FP64)
 //   residual partials        [S][chunks][2] FP64
 // MOM = 1 for isotropic scattering (phi), 3 for the linear kernel (phi, Jx, Jy).
+// 3D grids use the same arrays with K * J rows ([K][J][NXP] per sample); their
+// sweep accumulates phi of each sample directly into part [S][K][J][NXP].
 #pragma once
 
 #include <cuda_runtime.h>
@@ -20,9 +22,11 @@ namespace romk {
 constexpr int kCols = 8;       // cells per lane along x
 constexpr int kMaxG = 4;       // ordinates per sweep work item
 constexpr int kMaxWarps = 8;   // I <= 32 * 8 * 8 = 2048
+constexpr int kMaxCtaItems3 = 256;  // 3D: work items per CTA list
 
 // One sweep work item: up to kMaxG ordinates of one quadrant of one sample.
-// quad bit 0 set: c < 0 (sweep from x_R), bit 1 set: s < 0 (sweep from y_T).
+// quad bit 0 set: c < 0 (sweep from x_R), bit 1 set: s < 0 (sweep from y_T),
+// bit 2 set (3D): mu_z < 0 (sweep from z_T).
 struct SweepItem {
     int sample;
     int quad;
@@ -48,6 +52,7 @@ struct SweepArgs {
 
 struct CombineArgs {
     int S, MOM, chunks;
+    int zero_part;              // 1: one part array per sample, read and cleared (3D)
     long long cells4;           // J * NXP / 4
     long long cells;
     float g;                    // linear-kernel asymmetry (MOM = 3)
@@ -58,6 +63,30 @@ struct CombineArgs {
     const float *sigma_s, *q;
     const int *active;
     double *partials;           // [S][chunks][2]
+};
+
+// 3D sweep (K9): G = 1 or 2 ordinates of one sample and octant per work item,
+// CTAs over lists of items of one octant, x-y tiles swept by successive launches.
+struct Sweep3Args {
+    int I, J, K, NXP;
+    float inv_dx, inv_dy, inv_dz;
+    const float *sigma_t;       // [K][J][NXP]
+    const float *src;           // [S][K][J][NXP] isotropic source sigma_S phi + q
+    float *phi;                 // [S][K][J][NXP] flux accumulated by the sweep
+    const SweepItem *items;     // quad = octant bits, ord[0] the ordinate
+    const int *cta_begin;       // [n_ctas + 1] ranges of cta_list
+    const int *cta_list;        // item indices, one octant per CTA
+    const float *oc, *os, *oz, *ow;
+    const float *inflow;        // nullptr = vacuum; else [x_L: K*J][x_R: K*J][y_B: K*I][y_T: K*I]
+                                //                        [z_B: J*I][z_T: J*I]
+    long long inflow_stride;    // per ordinate (0 = same values for every ordinate)
+    const int *active;          // [S]
+    long long cells;            // K * J * NXP
+    int tile_x, tile_y;         // tile of this launch, counted from the inflow corner
+    int n_tx, n_ty;             // tiles along x and y
+    float *xface;               // [items][G][K][J] x-edges handed to the next x tile
+    float *yface;               // [items][G][K][NXP] y-edges handed to the next y tile
+    int *err;                   // bit 0/1: an mbarrier wait timed out
 };
 
 struct FinalizeArgs {
@@ -81,8 +110,9 @@ struct OrdGenArgs {
     const long long *ord_off;   // [S] first ordinate of the sample
     int first_sample;           // global index of local sample 0
     int total_cells;
+    int octants;                // 1: 3D sets, the 4 quadrants mirrored in zeta (8 m points)
     double *c64, *s64, *z64, *w64;
-    float *c32, *s32, *w32;
+    float *c32, *s32, *z32, *w32;
 };
 
 // Dense scattering operator A[l][l'] = w_l' P(u_l', u_l) per sample (K3).
@@ -150,6 +180,10 @@ __device__ __forceinline__ void stg8(float *p, const float (&v)[8])
 // source in, psi out).
 cudaError_t launch_sweep2d(const SweepArgs &a, int n_items, int nwarps, int G, int scheme,
                            bool homog, int mom, cudaStream_t st);
+cudaError_t launch_sweep3d(const Sweep3Args &a, int n_ctas, int nwarps, int G, int scheme,
+                           cudaStream_t st);
+int sweep3d_ctas_per_sm(int nwarps, int G);
+int sweep3d_tile_cols();  // x extent of a 3D tile (8-column strips x warps per CTA)
 cudaError_t launch_combine(const CombineArgs &a, cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t st);
 cudaError_t launch_init_state(int S, int MOM, long long cells, const float *q, float *phi,

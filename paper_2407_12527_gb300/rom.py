@@ -26,7 +26,7 @@ KERNEL = {"iso": 0, "linear": 1, "hg": 2}
 KERNEL_FLAG_NORMALIZE = 1
 KERNEL_FLAG_RAW = 2
 QUAD = {"uniform": 0, "gauss": 1, "product_gl": 2}
-FACES = {"xl": 0, "xr": 1, "yb": 2, "yt": 3}
+FACES = {"xl": 0, "xr": 1, "yb": 2, "yt": 3, "zb": 4, "zt": 5}
 
 
 class rom_options(ctypes.Structure):
@@ -78,6 +78,7 @@ SIGNATURES = {
     "rom_set_ordinates": (_i, [_vp, _i, _i32p, _dp, _dp]),
     "rom_set_ordinates_seed": (_i, [_vp, ctypes.c_uint64, _i, _i32p, _i32p]),
     "rom_set_ordinates_seed_offset": (_i, [_vp, ctypes.c_uint64, _i, _i, _i32p, _i32p]),
+    "rom_set_ordinates_seed_xyz": (_i, [_vp, ctypes.c_uint64, _i, _i, _i32p, _i32p]),
     "rom_set_quadrature": (_i, [_vp, _i, _i, _i]),
     "rom_quadrature_xy": (_i, [_i, _i, _i, _dp, _dp, _i32p]),
     "rom_get_ordinates": (_i, [_vp, _dp, _dp]),
@@ -148,6 +149,8 @@ class RomContext:
         if rc != ROM_OK:
             raise RomError(rc, f"rom_create(device={device}) failed (no usable CUDA device?)")
         self.I = self.J = 0
+        self.K = 1
+        self.dim = 2
         self.n_samples = 0
 
     def close(self):
@@ -188,7 +191,30 @@ class RomContext:
         st, ss, qq = (_f64(np.broadcast_to(a, (J, I))) for a in (sigma_t, sigma_s, q))
         self._check(self.L.rom_set_grid(self.h, 2, _ptr(n, _i64p), _ptr(lo), _ptr(hi), _ptr(st),
                                         _ptr(ss), _ptr(qq)), "rom_set_grid")
-        self.I, self.J = I, J
+        self.I, self.J, self.K, self.dim = I, J, 1, 2
+
+    def set_grid3(self, I, J, K, bounds, sigma_t, sigma_s, q):
+        """3D grid: bounds = (x_L, x_R, y_B, y_T, z_B, z_T); arrays [K, J, I]."""
+        n = np.array([I, J, K], dtype=np.int64)
+        lo = np.array([bounds[0], bounds[2], bounds[4]], dtype=np.float64)
+        hi = np.array([bounds[1], bounds[3], bounds[5]], dtype=np.float64)
+        st, ss, qq = (_f64(np.broadcast_to(a, (K, J, I))) for a in (sigma_t, sigma_s, q))
+        self._check(self.L.rom_set_grid(self.h, 3, _ptr(n, _i64p), _ptr(lo), _ptr(hi), _ptr(st),
+                                        _ptr(ss), _ptr(qq)), "rom_set_grid")
+        self.I, self.J, self.K, self.dim = I, J, K, 3
+
+    def set_grid3_device(self, I, J, K, bounds, sigma_t, sigma_s, q):
+        """sigma_t, sigma_s, q: contiguous float32 CUDA tensors [K, J, I] (torch)."""
+        for t in (sigma_t, sigma_s, q):
+            assert t.is_cuda and t.dtype.is_floating_point and t.element_size() == 4
+            assert t.is_contiguous() and tuple(t.shape) == (K, J, I)
+        n = np.array([I, J, K], dtype=np.int64)
+        lo = np.array([bounds[0], bounds[2], bounds[4]], dtype=np.float64)
+        hi = np.array([bounds[1], bounds[3], bounds[5]], dtype=np.float64)
+        self._check(self.L.rom_set_grid_device(self.h, 3, _ptr(n, _i64p), _ptr(lo), _ptr(hi),
+                                               _vp(sigma_t.data_ptr()), _vp(sigma_s.data_ptr()),
+                                               _vp(q.data_ptr())), "rom_set_grid_device")
+        self.I, self.J, self.K, self.dim = I, J, K, 3
 
     def set_grid_device(self, I, J, bounds, sigma_t, sigma_s, q):
         """sigma_t, sigma_s, q: contiguous float32 CUDA tensors [J, I] (torch)."""
@@ -201,7 +227,7 @@ class RomContext:
         self._check(self.L.rom_set_grid_device(self.h, 2, _ptr(n, _i64p), _ptr(lo), _ptr(hi),
                                                _vp(sigma_t.data_ptr()), _vp(sigma_s.data_ptr()),
                                                _vp(q.data_ptr())), "rom_set_grid_device")
-        self.I, self.J = I, J
+        self.I, self.J, self.K, self.dim = I, J, 1, 2
 
     def set_inflow_isotropic(self, face, values):
         f = FACES[face] if isinstance(face, str) else face
@@ -232,6 +258,15 @@ class RomContext:
                     "rom_set_ordinates_seed_offset")
         self.n_samples = int(nz.size)
 
+    def set_ordinates_seed_xyz(self, seed, n_zeta, n_theta, first_sample=0):
+        """3D sets: 8 n_zeta n_theta ordinates per sample (octants)."""
+        nz = np.ascontiguousarray(np.asarray(n_zeta, dtype=np.int32))
+        nt = np.ascontiguousarray(np.asarray(n_theta, dtype=np.int32))
+        self._check(self.L.rom_set_ordinates_seed_xyz(self.h, seed, first_sample, nz.size,
+                                                      _ptr(nz, _i32p), _ptr(nt, _i32p)),
+                    "rom_set_ordinates_seed_xyz")
+        self.n_samples = int(nz.size)
+
     def set_quadrature(self, kind, n1, n2=0):
         self._check(self.L.rom_set_quadrature(self.h, QUAD[kind], n1, n2), "rom_set_quadrature")
         self.n_samples = 1
@@ -256,13 +291,16 @@ class RomContext:
         d["status"] = rc
         return d
 
+    def _shape(self):
+        return (self.K, self.J, self.I) if self.dim == 3 else (self.J, self.I)
+
     def scalar_flux(self, sample=-1) -> np.ndarray:
-        out = np.zeros((self.J, self.I))
+        out = np.zeros(self._shape())
         self._check(self.L.rom_get_scalar_flux(self.h, sample, _ptr(out)), "rom_get_scalar_flux")
         return out
 
     def scalar_flux_device(self, out_tensor, sample=-1):
-        """Write phi into a float64 CUDA tensor [J, I] on the context stream."""
+        """Write phi into a float64 CUDA tensor [J, I] ([K, J, I]) on the context stream."""
         assert out_tensor.is_cuda and out_tensor.element_size() == 8 and out_tensor.is_contiguous()
         self._check(self.L.rom_get_scalar_flux_device(self.h, sample, _vp(out_tensor.data_ptr())),
                     "rom_get_scalar_flux_device")
@@ -275,7 +313,7 @@ class RomContext:
         return it, r
 
     def partial_sum(self):
-        s = np.zeros((self.J, self.I))
+        s = np.zeros(self._shape())
         n = ctypes.c_int64(0)
         self._check(self.L.rom_get_partial_sum(self.h, _ptr(s), ctypes.byref(n)),
                     "rom_get_partial_sum")

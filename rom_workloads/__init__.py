@@ -19,6 +19,12 @@ Workloads (all synthetic; the paper uses no datasets):
     uniformly from {8, 16, 32, 64}.
   * ``hg_disc``       -- 512 x 512 on [0,1]^2, sigma_T = 1, sigma_S = 0.95, Henyey-
     Greenstein g = 0.8, q = 1 where |z - (0.5,0.5)| <= 0.05; 32 samples x 128.
+  * ``lognormal_cube`` -- 3D, 128^3 on [0,1]^3, sigma_T = exp(-0.125 + 0.5 G) with G a
+    unit-variance Gaussian random field (white noise from a seeded PCG64 stream,
+    convolved by FFT with a Gaussian of standard deviation 8/sqrt(2) cells, i.e.
+    covariance exp(-r^2 / (2 * 8^2)), periodic), so E[sigma_T] = 1; sigma_S =
+    0.8 sigma_T; q = 1 on the central 8^3 cells (60..67); vacuum; 64 samples x 48
+    ordinates (8 octants x 2 x 3 cells).
 """
 from __future__ import annotations
 
@@ -115,6 +121,51 @@ def hg_disc(n: int = 512, n_samples: int = 32, m_quadrant: int = 32) -> Problem2
                                 "m_quadrant": [m_quadrant] * n_samples})
 
 
+@dataclass
+class Problem3D:
+    name: str
+    I: int
+    J: int
+    K: int
+    bounds: tuple  # (x_L, x_R, y_B, y_T, z_B, z_T)
+    sigma_t: np.ndarray  # [K, J, I]
+    sigma_s: np.ndarray
+    q: np.ndarray
+    ordinates: dict = field(default_factory=dict)
+
+    @property
+    def n_cells(self) -> int:
+        return self.I * self.J * self.K
+
+
+def gaussian_random_field(n: int, corr_cells: float, seed: int) -> np.ndarray:
+    """Periodic unit-variance Gaussian field on n^3 cells with covariance
+    exp(-r^2 / (2 corr^2)): white noise convolved (FFT) with a Gaussian of standard
+    deviation corr / sqrt(2) cells, then centred and scaled to unit variance."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    noise = rng.standard_normal((n, n, n))
+    d = np.minimum(np.arange(n), n - np.arange(n)).astype(np.float64)
+    s2 = (corr_cells / np.sqrt(2.0)) ** 2
+    g1 = np.exp(-d * d / (2.0 * s2))
+    kern = g1[:, None, None] * g1[None, :, None] * g1[None, None, :]
+    field_ = np.fft.irfftn(np.fft.rfftn(noise) * np.fft.rfftn(kern), s=noise.shape)
+    field_ -= field_.mean()
+    return field_ / field_.std()
+
+
+def lognormal_cube(n: int = 128, n_samples: int = 64, n_zeta: int = 2, n_theta: int = 3,
+                   seed: int = 5000) -> Problem3D:
+    G = gaussian_random_field(n, 8.0, seed)
+    sigma_t = np.exp(-0.125 + 0.5 * G)
+    q = np.zeros((n, n, n))
+    c0 = n // 2 - 4
+    q[c0:c0 + 8, c0:c0 + 8, c0:c0 + 8] = 1.0
+    return Problem3D(f"lognormal_cube_{n}", n, n, n, (0.0, 1.0, 0.0, 1.0, 0.0, 1.0), sigma_t,
+                     0.8 * sigma_t, q,
+                     ordinates={"kind": "rom3", "n_samples": n_samples,
+                                "n_zeta": [n_zeta] * n_samples, "n_theta": [n_theta] * n_samples})
+
+
 # ------------------------------------------------------- random test inputs
 
 def random_medium(I: int, J: int, seed: int, ratio_max: float = 0.9,
@@ -143,6 +194,36 @@ def random_directions(M: int, seed: int, weights: str = "equal"):
         w = rng.uniform(0.5, 1.5, size=M)
         w /= w.sum()
     return rho * np.cos(th), rho * np.sin(th), zeta, w
+
+
+def random_directions_sphere(M: int, seed: int, weights: str = "equal"):
+    """M directions uniform on the whole unit sphere (mu_z ~ U(-1,1), azimuth ~
+    U(0, 2 pi)) as (c, s, mu_z, w), FP64; weights equal or random positive, sum 1."""
+    rng = np.random.default_rng(seed)
+    mz = rng.uniform(-1.0, 1.0, size=M)
+    th = rng.uniform(0.0, 2.0 * np.pi, size=M)
+    rho = np.sqrt(1.0 - mz * mz)
+    if weights == "equal":
+        w = np.full(M, 1.0 / M)
+    else:
+        w = rng.uniform(0.5, 1.5, size=M)
+        w /= w.sum()
+    return rho * np.cos(th), rho * np.sin(th), mz, w
+
+
+def random_medium3(I: int, J: int, K: int, seed: int, ratio_max: float = 0.9,
+                   sigma_t_range=(0.5, 4.0), q_max: float = 2.0):
+    """3D heterogeneous sigma_T, sigma_S <= ratio_max * sigma_T, q >= 0 ([K, J, I])."""
+    rng = np.random.default_rng(seed)
+    st = rng.uniform(*sigma_t_range, size=(K, J, I))
+    ss = st * rng.uniform(0.0, ratio_max, size=(K, J, I))
+    q = rng.uniform(0.0, q_max, size=(K, J, I))
+    return st, ss, q
+
+
+def face_sizes3(I: int, J: int, K: int):
+    """Cells of the six faces in the order x_L, x_R, y_B, y_T, z_B, z_T."""
+    return [K * J, K * J, K * I, K * I, J * I, J * I]
 
 
 def random_inflow(I: int, J: int, seed: int, per_ordinate_M: int = 0, scale: float = 1.0):
