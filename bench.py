@@ -38,6 +38,7 @@ METRIC = "cell-ordinate updates/s (ROM source iteration, 1 GB300)"
 UNIT = "updates/s"
 FLOP_PER_UPDATE = 11  # diamond difference, homogeneous sigma_T: 5 FMA + 1 MUL
 FLOP_PER_UPDATE_HET = 13  # heterogeneous sigma_T: + 1 add + 1 reciprocal per cell-ordinate
+FLOP_PER_UPDATE_3D = 17   # 3D, heterogeneous: 3 FMA + add + reciprocal + MUL, 3 FMA outflows, 1 FMA phi
 TOL = 1e-6
 
 
@@ -51,6 +52,11 @@ class Workload:
         self.nz, self.nt, self.quad = nz, nt, quad
         self.kernel, self.g = kernel, g
         self.seed = W.ordinate_seed(cfg_index)
+        self.dim = 3 if hasattr(problem, "K") else 2
+
+    @property
+    def cells(self):
+        return self.p.I * self.p.J * (self.p.K if self.dim == 3 else 1)
 
     @property
     def samples(self):
@@ -60,7 +66,8 @@ class Workload:
         if self.quad:
             from paper_2407_12527_gb300 import quadrature_xy
             return quadrature_xy(*self.quad)[0].shape[0]
-        return int(sum(4 * a * b for a, b in zip(self.nz, self.nt)))
+        per = 8 if self.dim == 3 else 4
+        return int(sum(per * a * b for a, b in zip(self.nz, self.nt)))
 
 
 def make_workload(name):
@@ -92,6 +99,13 @@ def make_workload(name):
                         "g=0.8, q=1 in a disc r<=0.05): ROM 32 samples x 128 ordinates, dense "
                         "operator (FP32 GEMM), SI to 1e-6", nz=[4] * 32, nt=[8] * 32,
                         kernel="hg", g=0.8, cfg_index=3)
+    if name == "lognormal_cube":
+        p = W.lognormal_cube()
+        o = p.ordinates
+        return Workload(name, p, "lognormal_cube_128 (128^3 on [0,1]^3, sigma_T lognormal mean 1, "
+                        "log-std 0.5, correlation 8 cells; sigma_S=0.8 sigma_T isotropic; q=1 on "
+                        "the central 8^3; vacuum): ROM 64 samples x 48 ordinates (8 octants x 2 x 3), "
+                        "SI to 1e-6", nz=o["n_zeta"], nt=o["n_theta"], cfg_index=4)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -101,7 +115,8 @@ WL = None  # the workload of this run (set in main)
 def workload_config(extra=None):
     p = WL.p
     cfg = {
-        "workload": WL.desc, "grid": [p.I, p.J], "samples_per_step": WL.samples,
+        "workload": WL.desc, "grid": [p.I, p.J] + ([p.K] if WL.dim == 3 else []),
+        "samples_per_step": WL.samples,
         "ordinates_per_step": WL.m_total(), "si_tol": TOL, "scheme": "diamond difference",
         "kernel": WL.kernel + (f" g={WL.g}" if WL.g else ""),
         "l2": "flushed between steps (256 MiB write outside the timed events)",
@@ -214,7 +229,8 @@ def oracle_sets(first: int, count: int):
                  "product_gl": lambda: O.quad_product_gl_xy(n1, n2)}[kind]
         return [maker()]
     S = WL.samples
-    return [O.rom_ordinates_xy(WL.seed, first + k, WL.nz[(first + k) % S], WL.nt[(first + k) % S])
+    gen = O.rom_ordinates_xyz if WL.dim == 3 else O.rom_ordinates_xy
+    return [gen(WL.seed, first + k, WL.nz[(first + k) % S], WL.nt[(first + k) % S])
             for k in range(count)]
 
 
@@ -231,9 +247,13 @@ def oracle_rate(budget_s: float, max_samples: int, first: int = 0):
     while n < max_samples:
         o = oracle_sets(first + n, 1)[0]
         kw = {"fixed_iters": 1} if WL.kernel == "hg" else {"tol": TOL}
-        r = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, [o], kernel=WL.kernel,
-                       g=WL.g, allow_not_converged=True, **kw)
-        upd += p.I * p.J * o.M * int(r["iters"][0])
+        if WL.dim == 3:
+            r = O.solve_xyz(p.I, p.J, p.K, p.bounds, p.sigma_t, p.sigma_s, p.q, [o],
+                            allow_not_converged=True, **kw)
+        else:
+            r = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, [o], kernel=WL.kernel,
+                           g=WL.g, allow_not_converged=True, **kw)
+        upd += WL.cells * o.M * int(r["iters"][0])
         m_max = max(m_max, o.M)
         n += 1
         if time.perf_counter() - t0 > budget_s:
@@ -303,7 +323,10 @@ def run_ours(args):
     st_d, ss_d, q_d = (torch.tensor(a, dtype=torch.float32, device=dev).contiguous()
                        for a in (p.sigma_t, p.sigma_s, p.q))
     torch.cuda.synchronize(dev)
-    ctx.set_grid_device(p.I, p.J, p.bounds, st_d, ss_d, q_d)
+    if WL.dim == 3:
+        ctx.set_grid3_device(p.I, p.J, p.K, p.bounds, st_d, ss_d, q_d)
+    else:
+        ctx.set_grid_device(p.I, p.J, p.bounds, st_d, ss_d, q_d)
     setup(ctx)
     ctx.set_options(tol=TOL, check_every=args.check_every, tile_g=args.tile_g)
 
@@ -315,6 +338,8 @@ def run_ours(args):
             if step == 0 or getattr(c, "_quad_set", False) is False:
                 c.set_quadrature(*WL.quad)
                 c._quad_set = True
+        elif WL.dim == 3:
+            c.set_ordinates_seed_xyz(WL.seed, WL.nz, WL.nt, first_sample=first_sample(step))
         else:
             c.set_ordinates_seed(WL.seed, WL.nz, WL.nt, first_sample=first_sample(step))
 
@@ -382,15 +407,15 @@ def run_ours(args):
     ctx.set_options(tol=TOL, check_every=args.check_every, tile_g=args.tile_g)
     peak_tflops = 152 * 128 * 2 * 2070e6 / 1e12
     homog = float(np.min(p.sigma_t)) == float(np.max(p.sigma_t))
-    fpu = FLOP_PER_UPDATE if homog else FLOP_PER_UPDATE_HET
+    fpu = FLOP_PER_UPDATE_3D if WL.dim == 3 else (FLOP_PER_UPDATE if homog else FLOP_PER_UPDATE_HET)
     if WL.kernel == "hg" and src_ms > 0:
         achieved = src_flop / (src_ms / 1e3) / 1e12
         kernel_name, n_l, avg_us, fu = ("dense_source_kernel (K4, FP32 SIMT GEMM)", src_n,
                                         1e3 * src_ms / max(src_n, 1), None)
     else:
         achieved = sweep_upd * fpu / (sweep_ms / 1e3) / 1e12
-        kernel_name, n_l, avg_us, fu = ("sweep2d_kernel (K1)", sweep_n,
-                                        1e3 * sweep_ms / max(sweep_n, 1), fpu)
+        kernel_name = "sweep3d_kernel (K9)" if WL.dim == 3 else "sweep2d_kernel (K1)"
+        kernel_name, n_l, avg_us, fu = (kernel_name, sweep_n, 1e3 * sweep_ms / max(sweep_n, 1), fpu)
     # DRAM bytes of one full sweep launch from the committed ncu capture, used
     # only while the sweep source is the one that was captured
     traffic = None
@@ -422,7 +447,10 @@ def run_ours(args):
     for k in range(args.warmup + args.steps):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        ctx2.set_grid(p.I, p.J, p.bounds, st_h, ss_h, q_h)
+        if WL.dim == 3:
+            ctx2.set_grid3(p.I, p.J, p.K, p.bounds, st_h, ss_h, q_h)
+        else:
+            ctx2.set_grid(p.I, p.J, p.bounds, st_h, ss_h, q_h)
         ctx2._quad_set = False
         set_ordinates(ctx2, k)
         s = ctx2.solve(allow_not_converged=True)
@@ -435,7 +463,7 @@ def run_ours(args):
     e2e_t = barrier_max(e2e_t, world, dev)
     e2e_upd = barrier_sum(float(e2e_upd), world, dev)
     e2e = {"value": e2e_upd / e2e_t, "unit": UNIT,
-           "h2d_bytes_per_step": 3 * p.I * p.J * 8, "d2h_bytes_per_step": p.I * p.J * 8}
+           "h2d_bytes_per_step": 3 * WL.cells * 8, "d2h_bytes_per_step": WL.cells * 8}
     ctx2.close()
     ctx.close()
 
@@ -581,7 +609,7 @@ def main():
                     help="CPU seconds the reference (oracle) arm spends over all its steps")
     ap.add_argument("--workload", default="point_source",
                     choices=["point_source", "point_source_dom", "dom_small", "checkerboard",
-                             "hg_disc"])
+                             "hg_disc", "lognormal_cube"])
     ap.add_argument("--rom-vs-dom", action="store_true",
                     help="measure GPU time to a relative l2 error target, ROM vs plain DOM")
     ap.add_argument("--target", type=float, default=1e-3)

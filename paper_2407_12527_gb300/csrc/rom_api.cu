@@ -1268,8 +1268,13 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
         if ((rc = upload_inflow(ctx))) return rc;
         invalidate_graph(ctx);
     }
-    // residual chunks: blocks of 256 threads with one 8-cell sector each
-    const int chunks = (int)std::max<long long>(1, (cells / 8 + 255) / 256);
+    // residual chunks: combine blocks of 256 threads per sample, each thread
+    // taking one or more 8-cell sectors; about 16 blocks per SM in all, so that
+    // large grids stream many sectors per thread instead of paying the block's
+    // FP64 reduction per sector, and the finalize adds few partials per sample
+    const long long max_chunks = std::max<long long>(1, (cells / 8 + 255) / 256);
+    const long long want = std::max<long long>(1, (16LL * ctx->sm_count + ctx->S - 1) / ctx->S);
+    const int chunks = (int)std::min(max_chunks, want);
     if (chunks != ctx->chunks) invalidate_graph(ctx);
     ctx->chunks = chunks;
     const int MOM = ctx->MOM == 0 ? 1 : ctx->MOM;  // moments kept per sample

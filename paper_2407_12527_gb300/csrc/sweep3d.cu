@@ -147,6 +147,65 @@ __device__ __forceinline__ void red8(float *p, const float (&v)[kCols])
                  : "memory");
 }
 
+// One step of a lane: its 4 x 8 block for the G ordinates of the item.  The
+// cells are taken by anti-diagonals of the block (cell (h, r) at diagonal h + r,
+// r counted from the x inflow side), so the up to four cells of a diagonal are
+// independent and their dependent FMA chains overlap.  A row's flux goes out
+// (one vector reduction per 4 cells) as soon as the row is done, and its source
+// and sigma_T registers are reloaded with the row of the next step.
+template <int G, int SCHEME, bool XNEG, bool CHECK>
+__device__ __forceinline__ void block_diag(
+    const typename V3<G>::T a, const typename V3<G>::T b, const typename V3<G>::T e,
+    const typename V3<G>::T abe, const typename V3<G>::T wg, const typename V3<G>::T (&xin)[kH3],
+    typename V3<G>::T (&y)[kCols], typename V3<G>::T (&z)[kH3][kCols], float (&pS)[kH3][kCols],
+    float (&pT)[kH3][kCols], const bool (&rok)[kH3], const bool (&cok)[kCols], float *phi_k,
+    const float *sp2, const float *tp2, const int (&jrow)[kH3], int NXP, bool act2,
+    typename V3<G>::T (&xo)[kH3])
+{
+    using T = typename V3<G>::T;
+    T x[kH3];
+    float out[kH3][kCols];
+#pragma unroll
+    for (int h = 0; h < kH3; ++h) x[h] = xin[h];
+#pragma unroll
+    for (int d = 0; d < kCols + kH3 - 1; ++d) {
+#pragma unroll
+        for (int h = 0; h < kH3; ++h) {
+            const int rr = d - h;
+            if (rr < 0 || rr >= kCols) continue;
+            const int r = XNEG ? kCols - 1 - rr : rr;
+            if (CHECK && !(rok[h] && cok[r])) {
+                out[h][r] = 0.f;
+                continue;
+            }
+            const T num = vfma(a, x[h], vfma(b, y[r], vfma(e, z[h][r], vsplat<T>(pS[h][r]))));
+            const T pc = vmul(num, vrcp(vadd(vsplat<T>(pT[h][r]), abe)));
+            if (SCHEME == 0) {
+                const T two = vsplat<T>(2.f);
+                x[h] = vfma(two, pc, vneg(x[h]));
+                y[r] = vfma(two, pc, vneg(y[r]));
+                z[h][r] = vfma(two, pc, vneg(z[h][r]));
+            } else {
+                x[h] = pc;
+                y[r] = pc;
+                z[h][r] = pc;
+            }
+            out[h][r] = wsum(wg, pc);
+        }
+        const int hf = d - (kCols - 1);  // the row finished at this diagonal
+        if (hf >= 0 && hf < kH3) {
+            xo[hf] = x[hf];
+            if (!CHECK || rok[hf]) {
+                red8(phi_k + (long long)jrow[hf] * NXP, out[hf]);
+                if (act2) {
+                    ldg8_early(sp2 + (long long)jrow[hf] * NXP, pS[hf]);
+                    ldg8_early(tp2 + (long long)jrow[hf] * NXP, pT[hf]);
+                }
+            }
+        }
+    }
+}
+
 template <int G, int SCHEME, bool XNEG>
 __device__ __forceinline__ void sweep3_body(const Sweep3Args &A, Smem3 &sm, int oct)
 {
@@ -183,6 +242,8 @@ __device__ __forceinline__ void sweep3_body(const Sweep3Args &A, Smem3 &sm, int 
     bool cok[kCols];
 #pragma unroll
     for (int r = 0; r < kCols; ++r) cok[r] = col0 + r < I;
+    // warp-uniform: every lane's block is 4 full rows of 8 valid cells
+    const bool full = col0 + kCols <= I && nrows % kH3 == 0;
 
     T a = vsplat<T>(0.f), b = a, e = a, abe = vsplat<T>(1.f), wg = a;
     float *phip = A.phi;
@@ -314,37 +375,21 @@ __device__ __forceinline__ void sweep3_body(const Sweep3Args &A, Smem3 &sm, int 
         const float *tp2 = A.sigma_t + off2;
         T xo[kH3];
         const long long pk = (long long)k * plane + col0;
+        if (act) {
+            if (full)
+                block_diag<G, SCHEME, XNEG, false>(a, b, e, abe, wg, xin, y, z, pS, pT, rok, cok,
+                                                    phip + pk, sp2, tp2, jrow, NXP, act2, xo);
+            else
+                block_diag<G, SCHEME, XNEG, true>(a, b, e, abe, wg, xin, y, z, pS, pT, rok, cok,
+                                                   phip + pk, sp2, tp2, jrow, NXP, act2, xo);
+        } else {
 #pragma unroll
-        for (int h = 0; h < kH3; ++h) {
-            xo[h] = vsplat<T>(0.f);
-            if (act && rok[h]) {
-                T x = xin[h];
-                float out[kCols];
-#pragma unroll
-                for (int rr = 0; rr < kCols; ++rr) {
-                    const int r = XNEG ? kCols - 1 - rr : rr;
-                    out[r] = 0.f;
-                    if (!cok[r]) continue;
-                    const T num = vfma(a, x, vfma(b, y[r], vfma(e, z[h][r], vsplat<T>(pS[h][r]))));
-                    const T pc = vmul(num, vrcp(vadd(vsplat<T>(pT[h][r]), abe)));
-                    if (SCHEME == 0) {
-                        const T two = vsplat<T>(2.f);
-                        x = vfma(two, pc, vneg(x));
-                        y[r] = vfma(two, pc, vneg(y[r]));
-                        z[h][r] = vfma(two, pc, vneg(z[h][r]));
-                    } else {
-                        x = pc;
-                        y[r] = pc;
-                        z[h][r] = pc;
-                    }
-                    out[r] = wsum(wg, pc);
+            for (int h = 0; h < kH3; ++h) {
+                xo[h] = vsplat<T>(0.f);
+                if (act2 && rok[h]) {
+                    ldg8_early(sp2 + (long long)jrow[h] * NXP, pS[h]);
+                    ldg8_early(tp2 + (long long)jrow[h] * NXP, pT[h]);
                 }
-                xo[h] = x;
-                red8(phip + pk + (long long)jrow[h] * NXP, out);
-            }
-            if (act2 && rok[h]) {
-                ldg8_early(sp2 + (long long)jrow[h] * NXP, pS[h]);
-                ldg8_early(tp2 + (long long)jrow[h] * NXP, pT[h]);
             }
         }
         // outgoing x-edges to the next strip (or the next tile)
