@@ -97,6 +97,10 @@ typedef struct rom_options {
     int dense_source;/* 0: the scattering source from angular moments when the kernel has  */
                      /* them (isotropic; linear without flags), else from the dense        */
                      /* M x M operator; 1: always the dense operator                       */
+    int dense_precision; /* the dense operator's product: 0 FP32 (CUDA cores); 1 split     */
+                     /* BF16 on the tensor cores (tcgen05: A_hi Psi_hi + A_hi Psi_lo +     */
+                     /* A_lo Psi_hi, FP32 accumulate; psi kept as BF16 hi/lo, same bytes;  */
+                     /* at most 128 ordinates per sample, else ROM_ERR_UNSUPPORTED)        */
 } rom_options;
 
 /* Statistics of the last rom_solve. */

@@ -96,9 +96,13 @@ struct rom_ctx {
     DevBuf cta_begin_dev, cta_list_dev, xface, yface, err3;
     int n_ctas3 = 0, nwarps3 = 1, n_tx = 1, n_ty = 1;
 
-    // dense scattering operator (mode 0)
-    DevBuf psi, src_ord, Amat, dtab;
+    // dense scattering operator (mode 0); tensor-core variant: split BF16 psi and A
+    DevBuf psi, src_ord, Amat, dtab, psi_hi, psi_lo, a_hi, a_lo, tc_err;
     bool pmat_dirty = true;
+    romk::DenseTcMaps tc_maps;
+    const void *tc_map_ptrs[4] = {nullptr, nullptr, nullptr, nullptr};
+    long long tc_map_cells = 0, tc_map_mtot = 0;
+    int tc_map_S = 0;
 
     // iteration state
     int MOM = 1;  // 1 isotropic moments, 3 linear moments, 0 dense operator
@@ -480,7 +484,12 @@ romk::SweepArgs sweep_args(const rom_ctx *ctx)
     a.cells = (long long)ctx->J * ctx->NXP;
     if (ctx->MOM == 0) {
         a.src = (const float *)ctx->src_ord.p;
-        a.psi = (float *)ctx->psi.p;
+        if (ctx->opt.dense_precision == 1) {
+            a.psi_hi = ctx->psi_hi.p;
+            a.psi_lo = ctx->psi_lo.p;
+        } else {
+            a.psi = (float *)ctx->psi.p;
+        }
     }
     return a;
 }
@@ -563,10 +572,34 @@ romk::DenseArgs dense_args(const rom_ctx *ctx)
 int prepare_dense(rom_ctx *ctx)
 {
     const long long cells = (long long)ctx->J * ctx->NXP;
+    const bool tc = ctx->opt.dense_precision == 1;
     int rc;
-    if ((rc = ensure(ctx, ctx->psi, (size_t)ctx->Mtot * cells * sizeof(float))) ||
-        (rc = ensure(ctx, ctx->src_ord, (size_t)ctx->Mtot * cells * sizeof(float))))
+    if (tc && max_m(ctx) > romk::dense_tc_max_m())
+        return fail(ctx, ROM_ERR_UNSUPPORTED,
+                    "dense_precision = 1 (tensor cores) needs at most %d ordinates per sample",
+                    romk::dense_tc_max_m());
+    if ((rc = ensure(ctx, ctx->src_ord, (size_t)ctx->Mtot * cells * sizeof(float)))) return rc;
+    if (tc) {
+        const size_t half = (size_t)ctx->Mtot * cells * 2;  // BF16
+        const size_t ab = (size_t)ctx->S * 128 * 128 * 2;
+        if ((rc = ensure(ctx, ctx->psi_hi, half)) || (rc = ensure(ctx, ctx->psi_lo, half)) ||
+            (rc = ensure(ctx, ctx->a_hi, ab)) || (rc = ensure(ctx, ctx->a_lo, ab)) ||
+            (rc = ensure(ctx, ctx->tc_err, sizeof(int))))
+            return rc;
+        const void *ptrs[4] = {ctx->a_hi.p, ctx->a_lo.p, ctx->psi_hi.p, ctx->psi_lo.p};
+        if (memcmp(ptrs, ctx->tc_map_ptrs, sizeof ptrs) != 0 || ctx->tc_map_cells != cells ||
+            ctx->tc_map_mtot != ctx->Mtot || ctx->tc_map_S != ctx->S) {
+            CK(romk::make_dense_tc_maps(&ctx->tc_maps, ctx->a_hi.p, ctx->a_lo.p, ctx->S,
+                                        ctx->psi_hi.p, ctx->psi_lo.p, ctx->Mtot, cells));
+            memcpy(ctx->tc_map_ptrs, ptrs, sizeof ptrs);
+            ctx->tc_map_cells = cells;
+            ctx->tc_map_mtot = ctx->Mtot;
+            ctx->tc_map_S = ctx->S;
+            invalidate_graph(ctx);
+        }
+    } else if ((rc = ensure(ctx, ctx->psi, (size_t)ctx->Mtot * cells * sizeof(float)))) {
         return rc;
+    }
     if (!ctx->pmat_dirty) return ROM_OK;
     std::vector<long long> a_off(ctx->S);
     long long asz = 0;
@@ -599,6 +632,11 @@ int prepare_dense(rom_ctx *ctx)
     pa.A = (float *)ctx->Amat.p;
     CK(romk::launch_pmat(pa, max_m(ctx), ctx->stream));
     ++ctx->launches;
+    if (tc) {  // A -> A_hi, A_lo (BF16, 128 x 128 per sample, zero padded)
+        CK(romk::launch_pmat_split((const float *)ctx->Amat.p, t.M, t.a_off, ctx->S, ctx->a_hi.p,
+                                   ctx->a_lo.p, ctx->stream));
+        ++ctx->launches;
+    }
     CK(cudaStreamSynchronize(ctx->stream));  // the host table dies with this call
     ctx->pmat_dirty = false;
     return ROM_OK;
@@ -652,7 +690,22 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     CK(romk::launch_combine(ca, st));
     if (ctx->MOM == 0) {
         if (k2) CK(cudaEventRecord(k2, st));
-        CK(romk::launch_dense_source(dense_args(ctx), max_m(ctx), st));
+        if (ctx->opt.dense_precision == 1) {
+            const romk::DenseArgs d = dense_args(ctx);
+            romk::DenseTcArgs ta{};
+            ta.S = ctx->S;
+            ta.M = d.M;
+            ta.ord_off = d.ord_off;
+            ta.cells = d.cells;
+            ta.sigma_s = d.sigma_s;
+            ta.q = d.q;
+            ta.src = d.src;
+            ta.active = d.active;
+            ta.err = (int *)ctx->tc_err.p;
+            CK(romk::launch_dense_tc(ctx->tc_maps, ta, ctx->sm_count, st));
+        } else {
+            CK(romk::launch_dense_source(dense_args(ctx), max_m(ctx), st));
+        }
         if (k3) CK(cudaEventRecord(k3, st));
     }
     romk::FinalizeArgs fa{};
@@ -771,6 +824,7 @@ void rom_default_options(rom_options *opt)
     opt->tile_g = 0;
     opt->time_kernels = 0;
     opt->dense_source = 0;
+    opt->dense_precision = 0;
 }
 
 int rom_create(rom_ctx **out, int cuda_device)
@@ -814,7 +868,8 @@ void rom_destroy(rom_ctx *ctx)
                       &ctx->active, &ctx->iters, &ctx->flags, &ctx->resid, &ctx->n_active,
                       &ctx->avg, &ctx->sum, &ctx->tmp, &ctx->psi, &ctx->src_ord, &ctx->Amat,
                       &ctx->dtab, &ctx->z32, &ctx->cta_begin_dev, &ctx->cta_list_dev,
-                      &ctx->xface, &ctx->yface, &ctx->err3};
+                      &ctx->xface, &ctx->yface, &ctx->err3, &ctx->psi_hi, &ctx->psi_lo,
+                      &ctx->a_hi, &ctx->a_lo, &ctx->tc_err};
     for (DevBuf *b : bufs) release(*b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -850,7 +905,10 @@ int rom_set_options(rom_ctx *ctx, const rom_options *opt)
         return fail(ctx, ROM_ERR_INVALID_ARG, "tile_g must be -1, 0, 1, 2 or 4");
     if (opt->dense_source != 0 && opt->dense_source != 1)
         return fail(ctx, ROM_ERR_INVALID_ARG, "dense_source must be 0 or 1");
-    if (opt->tile_g != ctx->opt.tile_g || opt->dense_source != ctx->opt.dense_source) {
+    if (opt->dense_precision != 0 && opt->dense_precision != 1)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "dense_precision must be 0 or 1");
+    if (opt->tile_g != ctx->opt.tile_g || opt->dense_source != ctx->opt.dense_source ||
+        opt->dense_precision != ctx->opt.dense_precision) {
         ctx->items_dirty = true;
         ctx->pmat_dirty = true;
     }
@@ -1312,6 +1370,8 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
 
     const long long launches0 = ctx->launches;
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    if (ctx->MOM == 0 && ctx->opt.dense_precision == 1)
+        CK(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), ctx->stream));
     if (ctx->dim == 3) {  // the sweep accumulates into part; the combine clears it
         CK(cudaMemsetAsync(ctx->part.p, 0, part_units * cells * sizeof(float), ctx->stream));
         CK(cudaMemsetAsync(ctx->err3.p, 0, sizeof(int), ctx->stream));
@@ -1380,9 +1440,12 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     ctx->h_iters.assign(ctx->S, 0);
     ctx->h_resid.assign(ctx->S, 0.0);
     std::vector<int> flags(ctx->S, 0);
-    int err3 = 0;
+    int err3 = 0, tc_err = 0;
     if (ctx->dim == 3)
         CK(cudaMemcpyAsync(&err3, ctx->err3.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    if (ctx->MOM == 0 && ctx->opt.dense_precision == 1)
+        CK(cudaMemcpyAsync(&tc_err, ctx->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost,
+                           ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_iters.data(), ctx->iters.p, ctx->S * sizeof(int),
                        cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_resid.data(), ctx->resid.p, ctx->S * sizeof(double),
@@ -1394,6 +1457,9 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
     if (err3)
         return fail(ctx, ROM_ERR_CUDA, "3D sweep: a wait between warps timed out (flags %d)", err3);
+    if (tc_err)
+        return fail(ctx, ROM_ERR_CUDA, "tensor-core dense source: a wait timed out (flags %d)",
+                    tc_err);
     ctx->solved = true;
 
     rom_stats st{};

@@ -14,6 +14,7 @@
 // sweep accumulates phi of each sample directly into part [S][K][J][NXP].
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -42,6 +43,8 @@ struct SweepArgs {
     const float *src;           // [S][MOM][J][NXP]; dense mode: [M_total][J][NXP] per ordinate
     float *part;                // [items][MOM][J][NXP] (dense mode: one moment, phi)
     float *psi;                 // dense mode: psi of every ordinate [M_total][J][NXP]
+    void *psi_hi, *psi_lo;      // dense mode, tensor cores: psi as BF16 hi / lo parts
+                                // [M_total][J][NXP] (psi unused when set)
     const SweepItem *items;
     const float *oc, *os, *ow;  // ordinate c, s, w
     const float *inflow;        // nullptr = vacuum; else face values [x_L:J][x_R:J][y_B:I][y_T:I]
@@ -140,6 +143,30 @@ struct DenseArgs {
     long long cells;
     const int *active;
 };
+
+// Dense source on the tensor cores (split BF16, tcgen05): TMA maps of A_hi,
+// A_lo [S][128][128] and Psi_hi, Psi_lo [M_total][cells] (BF16).
+struct DenseTcMaps {
+    CUtensorMap a_hi, a_lo, b_hi, b_lo;
+};
+struct DenseTcArgs {
+    int S;
+    const int *M;               // [S], each <= 128
+    const long long *ord_off;   // [S]
+    long long cells;            // a multiple of 8
+    const float *sigma_s, *q;
+    float *src;                 // [M_total][cells]
+    const int *active;
+    int *err;                   // bits 2..7: a wait timed out
+};
+int dense_tc_max_m();
+cudaError_t make_dense_tc_maps(DenseTcMaps *maps, const void *a_hi, const void *a_lo, int S,
+                               const void *psi_hi, const void *psi_lo, long long m_total,
+                               long long cells);
+cudaError_t launch_dense_tc(const DenseTcMaps &maps, const DenseTcArgs &a, int n_ctas,
+                            cudaStream_t st);
+cudaError_t launch_pmat_split(const float *A, const int *M, const long long *a_off, int S,
+                              void *hi, void *lo, cudaStream_t st);
 
 cudaError_t launch_pmat(const PmatArgs &a, int max_m, cudaStream_t st);
 cudaError_t launch_dense_source(const DenseArgs &a, int max_m, cudaStream_t st);

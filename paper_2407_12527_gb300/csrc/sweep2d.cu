@@ -27,6 +27,8 @@
 // block are loaded one step ahead into registers.  No ordinate or cell values
 // are stored: only the moments of each item, which a later kernel sums per
 // sample.
+#include <cuda_bf16.h>
+
 #include "rom_internal.cuh"
 
 namespace romk {
@@ -85,6 +87,24 @@ __device__ __forceinline__ float2 shfl1(float2 v)
 
 __device__ __forceinline__ void ld8(const float *__restrict__ p, float (&v)[kCols]) { ldg8_early(p, v); }
 __device__ __forceinline__ void st8(float *__restrict__ p, const float (&v)[kCols]) { stg8(p, v); }
+// psi of 8 cells as BF16 hi = bf16(v) and lo = bf16(v - hi), 16 bytes each
+__device__ __forceinline__ void st8_split(void *hi, void *lo, long long off, const float (&v)[kCols])
+{
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]);
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * e + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
+        h[e] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        l[e] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+    uint4 *ph = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(hi) + off);
+    uint4 *pl = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(lo) + off);
+    *ph = make_uint4(h[0], h[1], h[2], h[3]);
+    *pl = make_uint4(l[0], l[1], l[2], l[3]);
+}
 
 // Per-ordinate constants of a work item, grouped in packs.
 template <int G>
@@ -272,8 +292,11 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &A, int blk, bool yn
             st8(part_i + ra.base + h * ra.rs, v);
             if constexpr (MOM == 0) {
 #pragma unroll
-                for (int k = 0; k < G; ++k)
-                    st8(A.psi + (long long)o.ord[k] * A.cells + ra.base + h * ra.rs, psi_row[k]);
+                for (int k = 0; k < G; ++k) {
+                    const long long off = (long long)o.ord[k] * A.cells + ra.base + h * ra.rs;
+                    if (A.psi_hi) st8_split(A.psi_hi, A.psi_lo, off, psi_row[k]);
+                    else st8(A.psi + off, psi_row[k]);
+                }
             }
             if (MOM == 3) {
 #pragma unroll

@@ -33,7 +33,7 @@ class rom_options(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
                 ("fixed_iters", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("tile_g", ctypes.c_int), ("time_kernels", ctypes.c_int),
-                ("dense_source", ctypes.c_int)]
+                ("dense_source", ctypes.c_int), ("dense_precision", ctypes.c_int)]
 
 
 class rom_stats(ctypes.Structure):
