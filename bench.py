@@ -97,7 +97,7 @@ def make_workload(name):
         p = W.hg_disc()
         return Workload(name, p, "hg_disc_512 (512x512, sigma_T=1, sigma_S=0.95, Henyey-Greenstein "
                         "g=0.8, q=1 in a disc r<=0.05): ROM 32 samples x 128 ordinates, dense "
-                        "operator (FP32 GEMM), SI to 1e-6", nz=[4] * 32, nt=[8] * 32,
+                        "operator contraction per sweep, SI to 1e-6", nz=[4] * 32, nt=[8] * 32,
                         kernel="hg", g=0.8, cfg_index=3)
     if name == "lognormal_cube":
         p = W.lognormal_cube()
@@ -110,6 +110,7 @@ def make_workload(name):
 
 
 WL = None  # the workload of this run (set in main)
+ARGS = None  # the command line of this run
 
 
 def workload_config(extra=None):
@@ -119,6 +120,9 @@ def workload_config(extra=None):
         "samples_per_step": WL.samples,
         "ordinates_per_step": WL.m_total(), "si_tol": TOL, "scheme": "diamond difference",
         "kernel": WL.kernel + (f" g={WL.g}" if WL.g else ""),
+        "dense_product": (("split BF16 x3, tcgen05 tensor cores, FP32 accumulate"
+                           if ARGS.dense_precision == 1 else "FP32 CUDA cores")
+                          if WL.kernel == "hg" else None),
         "l2": "flushed between steps (256 MiB write outside the timed events)",
     }
     if extra:
@@ -180,6 +184,17 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(rows)}
+
+
+def measured_hbm_gbs():
+    """Measured copy bandwidth of this GPU pool (MEASURED_PEAKS.json), else the
+    fallback figure of an earlier GB300 measurement."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
 
 
 # ------------------------------------------------------------------ dist
@@ -328,7 +343,8 @@ def run_ours(args):
     else:
         ctx.set_grid_device(p.I, p.J, p.bounds, st_d, ss_d, q_d)
     setup(ctx)
-    ctx.set_options(tol=TOL, check_every=args.check_every, tile_g=args.tile_g)
+    ctx.set_options(tol=TOL, check_every=args.check_every, tile_g=args.tile_g,
+                    dense_precision=args.dense_precision)
 
     def first_sample(step):
         return (step * world + rank) * S
@@ -388,9 +404,10 @@ def run_ours(args):
 
     # roofline: the same steps with CUDA events around every sweep (and, for the dense
     # operator, every contraction) launch
-    ctx.set_options(tol=TOL, time_kernels=1, check_every=8, tile_g=args.tile_g)
+    ctx.set_options(tol=TOL, time_kernels=1, check_every=8, tile_g=args.tile_g,
+                    dense_precision=args.dense_precision)
     sweep_ms, sweep_upd, sweep_n, src_ms, src_n = 0.0, 0, 0, 0.0, 0
-    src_flop = 0.0
+    src_flop, src_bytes = 0.0, 0.0
     for k in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -404,11 +421,20 @@ def run_ours(args):
             it, _ = ctx.iterations()
             M = 4 * WL.nz[0] * WL.nt[0]
             src_flop += 2.0 * M * M * p.I * p.J * float(np.sum(it))
-    ctx.set_options(tol=TOL, check_every=args.check_every, tile_g=args.tile_g)
+            # algorithmic HBM bytes of a contraction: psi read + sources written, 4 B each
+            src_bytes += 8.0 * M * p.I * p.J * float(np.sum(it))
+    ctx.set_options(tol=TOL, check_every=args.check_every, tile_g=args.tile_g,
+                    dense_precision=args.dense_precision)
     peak_tflops = 152 * 128 * 2 * 2070e6 / 1e12
     homog = float(np.min(p.sigma_t)) == float(np.max(p.sigma_t))
     fpu = FLOP_PER_UPDATE_3D if WL.dim == 3 else (FLOP_PER_UPDATE if homog else FLOP_PER_UPDATE_HET)
-    if WL.kernel == "hg" and src_ms > 0:
+    hbm_peak = measured_hbm_gbs()
+    tc = WL.kernel == "hg" and args.dense_precision == 1
+    if WL.kernel == "hg" and src_ms > 0 and tc:
+        achieved = src_bytes / (src_ms / 1e3) / 1e9
+        kernel_name, n_l, avg_us, fu = ("dense_tc_kernel (K4, tcgen05 split BF16)", src_n,
+                                        1e3 * src_ms / max(src_n, 1), None)
+    elif WL.kernel == "hg" and src_ms > 0:
         achieved = src_flop / (src_ms / 1e3) / 1e12
         kernel_name, n_l, avg_us, fu = ("dense_source_kernel (K4, FP32 SIMT GEMM)", src_n,
                                         1e3 * src_ms / max(src_n, 1), None)
@@ -429,18 +455,31 @@ def run_ours(args):
             digest = hashlib.sha256(f.read()).hexdigest()
         if tr.get("sweep2d_cu_sha256") == digest:
             traffic = tr.get("dram_bytes_per_launch")
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": traffic,
-                "traffic_note": "DRAM read+write bytes of one full sweep launch (ncu)",
-                "kernel": kernel_name, "launches": n_l, "avg_launch_us": avg_us,
-                "flop_per_update": fu, "sweep_avg_launch_us": 1e3 * sweep_ms / max(sweep_n, 1),
-                "tile_g": s["tile_g"],
-                "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 flop x 2070 MHz"}
+    if tc and src_ms > 0:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": None,
+                    "traffic_note": "algorithmic bytes: psi (BF16 hi + lo) read and FP32 sources "
+                                    "written, 8 B per cell and ordinate",
+                    "kernel": kernel_name, "launches": n_l, "avg_launch_us": avg_us,
+                    "contraction_tflops": src_flop / (src_ms / 1e3) / 1e12,
+                    "sweep_avg_launch_us": 1e3 * sweep_ms / max(sweep_n, 1),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
+    else:
+        roofline = None
+    if roofline is None:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                    "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                    "traffic_note": "DRAM read+write bytes of one full sweep launch (ncu)",
+                    "kernel": kernel_name, "launches": n_l, "avg_launch_us": avg_us,
+                    "flop_per_update": fu,
+                    "sweep_avg_launch_us": 1e3 * sweep_ms / max(sweep_n, 1),
+                    "tile_g": s["tile_g"],
+                    "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 flop x 2070 MHz"}
 
     # end to end through the C ABI with host buffers
     ctx2 = RomContext(local)
     setup(ctx2)
-    ctx2.set_options(tol=TOL, tile_g=args.tile_g)
+    ctx2.set_options(tol=TOL, tile_g=args.tile_g, dense_precision=args.dense_precision)
     st_h, ss_h, q_h = (np.ascontiguousarray(a, dtype=np.float64) for a in
                        (p.sigma_t, p.sigma_s, p.q))
     e2e_upd, e2e_t = 0, 0.0
@@ -602,6 +641,9 @@ def main():
     ap.add_argument("--tile-g", type=int, default=-1,
                     help="ordinates per sweep work item (1, 2, 4; 0: size heuristic; "
                          "-1: measured by the library's autotuner)")
+    ap.add_argument("--dense-precision", type=int, default=1, choices=[0, 1],
+                    help="dense scattering operator product: 0 FP32 CUDA cores, 1 split BF16 "
+                         "on the tcgen05 tensor cores")
     ap.add_argument("--only-timed", action="store_true",
                     help="run the warm-up and timed steps only (no roofline, e2e or CPU legs)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -622,7 +664,8 @@ def main():
     ap.add_argument("--rom-batch", type=int, default=256)
     ap.add_argument("--rom-max", type=int, default=4096)
     args = ap.parse_args()
-    global WL
+    global WL, ARGS
+    ARGS = args
     if args.rom_vs_dom:
         return run_rom_vs_dom(args)
     WL = make_workload(args.workload)

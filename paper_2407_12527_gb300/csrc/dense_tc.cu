@@ -6,25 +6,30 @@
 // i.e. the product D = A Psi of the M x M operator with the M x cells matrix of
 // cell values, followed by the sigma_S / q epilogue.  M <= 128.
 //
-// Precision: split BF16.  Each FP32 value v is carried as v_hi = bf16(v) and
-// v_lo = bf16(v - v_hi) (16 significant bits in all), written that way by the
-// sweep (psi) and by pmat_split_kernel (A), and
+// Precision: split BF16.  Each FP32 value v is carried as v_hi = v rounded to
+// the nearest BF16 (ties away from zero) and v_lo = bf16_rn(v - v_hi) (16
+// significant bits in all), written that way by the sweep (psi, as one 32-byte
+// sector [8 hi | 8 lo] per 8 cells) and by pmat_split_kernel (A), and
 //   D = A_hi Psi_hi + A_hi Psi_lo + A_lo Psi_hi
 // is accumulated in FP32 in tensor memory; the dropped A_lo Psi_lo term is
-// below 2^-16 of each product.
+// below 2^-18 of each product and of either sign.
 //
 // GB300 mapping: one persistent CTA per SM walks a contiguous range of
 // (sample, 128-cell tile) units.  Warp 0 (one lane) is the TMA producer: the
 // sample's A_hi / A_lo (K-major, two 64-column boxes each) once per sample and,
-// per unit, the Psi_hi / Psi_lo tile (MN-major, two 64-cell boxes of 128 rows
-// each) into a two-stage ring, all with the 128-byte swizzle.  Warp 1 owns the
+// per unit, the Psi_hi / Psi_lo tile into a two-stage ring.  A is loaded with
+// the 128-byte swizzle; Psi, stored by the sweep as [row][8-cell group][hi | lo]
+// sectors, is loaded one 8-cell group x 128 rows box at a time (a 4D map over
+// [row][group][part][8], no swizzle), which lands as one column of 8 x 8 core
+// matrices of the canonical MN-major layout.  Warp 1 owns the
 // tensor memory (two 128 x 128 FP32 accumulators) and one lane issues, per
 // unit, 8 K-steps x 3 tcgen05.mma (kind::f16, BF16 in, FP32 accumulate, M = N =
 // 128), committing to mbarriers that free the Psi stage and hand the
 // accumulator to the epilogue.  Warps 2-5 read the accumulator (tcgen05.ld,
-// one TMEM lane per ordinate row), apply sigma_S and q and store the FP32
-// sources.  Every mbarrier wait is bounded; on timeout the CTA raises an error
-// flag, drains what it has in flight, frees its tensor memory and returns.
+// one TMEM lane per ordinate row), apply sigma_S and q (staged in shared memory
+// one unit ahead) and store the FP32 sources.  Every mbarrier wait is bounded;
+// on timeout the CTA raises an error flag, drains what it has in flight, frees
+// its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -50,9 +55,11 @@ struct TcBarriers {
     unsigned long long acc_full[2], acc_empty[2];
     uint32_t tmem_base;
     int abort_flag;
+    float sq[2][2][kTileN];  // sigma_S and q of a unit's cells, per accumulator buffer
 };
 // dynamic shared memory: [align pad][A 64 KB][B stage 0 64 KB][B stage 1 64 KB][barriers]
-constexpr uint32_t kSmemBytes = 1024 + kAbytes + kStages * kBbytes + 1024;
+constexpr uint32_t kSmemBytes = 1024 + kAbytes + kStages * kBbytes + 4096;
+static_assert(sizeof(TcBarriers) <= 4096, "barrier block");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -113,13 +120,25 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, int c3, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(smem_u32(bar))
+        : "memory");
+}
 
 // Shared-memory matrix descriptor of tcgen05: start address, leading and stride
-// byte offsets (16-byte units), descriptor version 1, 128-byte swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+// byte offsets (16-byte units), descriptor version 1, layout (bits 61-63: 0 no
+// swizzle, 2 128-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo,
+                                              uint32_t layout)
 {
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)layout << 61);
 }
 
 // Instruction descriptor, kind::f16: D FP32 (bits 4-5), A and B BF16 (bits 7-9,
@@ -253,10 +272,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_expect_tx(&bar->b_full[st], kBbytes);
                 const uint32_t dst = sB + st * kBbytes;
                 const int row0 = (int)a.ord_off[s], x0 = tile * kTileN;
-                for (int nb = 0; nb < 2; ++nb) {
-                    tma_load_2d(dst + nb * kBox, &maps.b_hi, x0 + 64 * nb, row0, &bar->b_full[st]);
-                    tma_load_2d(dst + (2 + nb) * kBox, &maps.b_lo, x0 + 64 * nb, row0,
-                                &bar->b_full[st]);
+                // part p (hi, lo) of group j: 128 rows x 16 B at dst + p * 32 KB + j * 2 KB
+                if (a.b_groups_per_box == kTileN / 8) {  // map with dims (e, row, part, group)
+                    for (int part = 0; part < 2; ++part)
+                        tma_load_4d(dst + part * 2 * kBox, &maps.b, 0, row0, part, x0 / 8,
+                                    &bar->b_full[st]);
+                } else {  // map with dims (e, part, group, row): one group per box
+                    for (int part = 0; part < 2; ++part)
+                        for (int j = 0; j < kTileN / 8; ++j)
+                            tma_load_4d(dst + part * 2 * kBox + j * 2048, &maps.b, 0, part,
+                                        x0 / 8 + j, row0, &bar->b_full[st]);
                 }
                 ++n_b;
             }
@@ -300,11 +325,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int ks = 0; ks < kK / 16; ++ks) {
                     // A: K-major, 128-byte rows of 64 k; the 16-wide K slice sits 32 B in
                     const uint32_t aoff = (ks >> 2) * kBox + (ks & 3) * 32;
-                    const uint64_t a_hi = smem_desc(sA + aoff, 16, 1024);
-                    const uint64_t a_lo = smem_desc(sA + 2 * kBox + aoff, 16, 1024);
-                    // B: MN-major, 8-row (k) atoms of 1024 B; the second 64-cell box at +16 KB
-                    const uint64_t b_hi = smem_desc(bb + ks * 2048, kBox, 1024);
-                    const uint64_t b_lo = smem_desc(bb + 2 * kBox + ks * 2048, kBox, 1024);
+                    const uint64_t a_hi = smem_desc(sA + aoff, 16, 1024, 2);
+                    const uint64_t a_lo = smem_desc(sA + 2 * kBox + aoff, 16, 1024, 2);
+                    // B: MN-major, no swizzle: 8 x 8 core matrices of 128 B, the next one
+                    // along K at +128 B (LBO), along the cells at +2 KB (SBO)
+                    const uint64_t b_hi = smem_desc(bb + ks * 256, 128, 2048, 0);
+                    const uint64_t b_lo = smem_desc(bb + 2 * kBox + ks * 256, 128, 2048, 0);
                     mma_bf16(d, a_hi, b_hi, ks > 0 ? 1u : 0u);
                     mma_bf16(d, a_hi, b_lo, 1u);
                     mma_bf16(d, a_lo, b_hi, 1u);
@@ -321,14 +347,48 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (n_b > 0) wait1(&bar->acc_full[(n_b - 1) & 1], (uint32_t)((n_b - 1) >> 1) & 1u);
         }
     } else {  // ------------------------------------------------------- epilogue (warps 2-5)
+        // Each thread holds one TMEM lane (an ordinate row) and writes 128 cells of it.
+        // sigma_S and q of a unit's 128 cells are staged in shared memory (one value
+        // per thread, loaded one unit ahead) and read back as broadcasts.
         const int g = warp & 3;  // TMEM lane quarter this warp may access
         const int row = 32 * g + lane;
+        const int et = threadIdx.x - 64;  // 0..127
         long long n_b = 0;
-        for (long long u = R.u0; u < R.u1; ++u) {
+        // first active unit of the range, and the sigma_S / q value this thread stages
+        long long un = R.u0;
+        while (un < R.u1 && !active_unit(un)) ++un;
+        auto fetch = [&](long long u, float &ssv, float &qv) {
+            ssv = qv = 0.f;
+            if (u < R.u1) {
+                const long long n = (u % n_tiles) * kTileN + et;
+                if (n < a.cells) {
+                    ssv = a.sigma_s[n];
+                    qv = a.q[n];
+                }
+            }
+        };
+        float ss_next, q_next;
+        fetch(un, ss_next, q_next);
+        for (long long u = un; u < R.u1; ++u) {
             if (!active_unit(u)) continue;
             const int s = (int)(u / n_tiles), tile = (int)(u % n_tiles);
             const int acc = (int)(n_b & 1);
-            if (!wait_warp(&bar->acc_full[acc], (uint32_t)(n_b >> 1) & 1u)) {
+            bar->sq[acc][0][et] = ss_next;
+            bar->sq[acc][1][et] = q_next;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            long long u2 = u + 1;
+            while (u2 < R.u1 && !active_unit(u2)) ++u2;
+            fetch(u2, ss_next, q_next);
+            const bool ok = wait_warp(&bar->acc_full[acc], (uint32_t)(n_b >> 1) & 1u);
+            // the four epilogue warps leave together or not at all (they share a named barrier)
+            uint32_t any_fail;
+            asm volatile(
+                "{\n\t.reg .pred p, q;\n\tsetp.eq.u32 p, %1, 0;\n\t"
+                "bar.red.or.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+                : "=r"(any_fail)
+                : "r"(ok ? 1u : 0u)
+                : "memory");
+            if (any_fail) {
                 if (lane == 0) atomicOr(a.err, 128);
                 break;
             }
@@ -336,6 +396,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int M = a.M[s];
             const long long n0 = (long long)tile * kTileN;
             float *dst = a.src + ((long long)a.ord_off[s] + row) * a.cells;
+            const float *sss = bar->sq[acc][0], *sqq = bar->sq[acc][1];
 #pragma unroll 1
             for (int c = 0; c < kTileN / 32; ++c) {
                 float v[32];
@@ -346,12 +407,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int q8 = 0; q8 < 4; ++q8) {
                         const long long n = nc + 8 * q8;
                         if (n < a.cells) {
-                            float ss[8], qq[8], out[8];
-                            ldg8(a.sigma_s + n, ss);
-                            ldg8(a.q + n, qq);
+                            float out[8];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e)
-                                out[e] = fmaf(ss[e], v[8 * q8 + e], qq[e]);
+                            for (int e = 0; e < 8; ++e) {
+                                const int j = 32 * c + 8 * q8 + e;
+                                out[e] = fmaf(sss[j], v[8 * q8 + e], sqq[j]);
+                            }
                             stg8(dst + n, out);
                         }
                     }
@@ -383,10 +444,10 @@ __global__ void pmat_split_kernel(const float *A, const int *Ms, const long long
     for (int i = threadIdx.x; i < kK * kK; i += blockDim.x) {
         const int l = i / kK, lp = i % kK;
         const float v = (l < M && lp < M) ? A[a_off[s] + (long long)l * M + lp] : 0.f;
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        const __nv_bfloat16 r = __float2bfloat16_rn(v - __bfloat162float(h));
-        hi[(long long)s * kK * kK + i] = h;
-        lo[(long long)s * kK * kK + i] = r;
+        const uint32_t b = (__float_as_uint(v) + 0x8000u) & 0xFFFF0000u;
+        const float vh = __uint_as_float(b);
+        hi[(long long)s * kK * kK + i] = __ushort_as_bfloat16((unsigned short)(b >> 16));
+        lo[(long long)s * kK * kK + i] = __float2bfloat16_rn(v - vh);
     }
 }
 
@@ -409,6 +470,39 @@ EncodeFn encode_fn()
             (void)cudaGetLastError();
     }
     return fn;
+}
+
+// 4D BF16 maps over the split psi [rows][cells / 8][2][8], no swizzle, zero fill
+// outside the tensor.  Preferred: dimensions listed as (element, row, part,
+// group), a box of 8 x 128 rows x 1 part x 16 groups landing as [group][row][8]
+// (16 core-matrix columns, 32 KB); returns 16 groups per box.  If the driver
+// refuses that order: dimensions (element, part, group, row), a box of one group
+// (128 rows x 16 bytes); returns 1.  0 on failure.
+int make_map_split(CUtensorMap *m, const void *ptr, unsigned long long cells,
+                   unsigned long long rows)
+{
+    EncodeFn fn = encode_fn();
+    if (!fn) return 0;
+    {
+        const cuuint64_t dims[4] = {8, rows, 2, cells / 8};
+        const cuuint64_t strides[3] = {cells * 4, 16, 32};
+        const cuuint32_t box[4] = {8, 128, 1, kTileN / 8};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(ptr), dims, strides,
+               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+            return kTileN / 8;
+    }
+    const cuuint64_t dims[4] = {8, 2, cells / 8, rows};
+    const cuuint64_t strides[3] = {16, 32, cells * 4};
+    const cuuint32_t box[4] = {8, 1, 1, 128};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(ptr), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS
+               ? 1
+               : 0;
 }
 
 // 2D BF16 map over [rows][cols] (cols contiguous), 64 x 128 boxes, 128-byte swizzle,
@@ -439,8 +533,8 @@ cudaError_t launch_pmat_split(const float *A, const int *M, const long long *a_o
 }
 
 cudaError_t make_dense_tc_maps(DenseTcMaps *maps, const void *a_hi, const void *a_lo, int S,
-                               const void *psi_hi, const void *psi_lo, long long m_total,
-                               long long cells)
+                               const void *psi_split, long long m_total, long long cells,
+                               int *b_groups_per_box)
 {
     if ((cells % 8) != 0 || m_total < 1 || S < 1) return cudaErrorInvalidValue;
     // the kernel's shared memory (set on the current device, outside any capture)
@@ -450,8 +544,8 @@ cudaError_t make_dense_tc_maps(DenseTcMaps *maps, const void *a_hi, const void *
     if (e != cudaSuccess) return e;
     if (!make_map(&maps->a_hi, a_hi, kK, (unsigned long long)S * kK) ||
         !make_map(&maps->a_lo, a_lo, kK, (unsigned long long)S * kK) ||
-        !make_map(&maps->b_hi, psi_hi, (unsigned long long)cells, (unsigned long long)m_total) ||
-        !make_map(&maps->b_lo, psi_lo, (unsigned long long)cells, (unsigned long long)m_total))
+        !(*b_groups_per_box = make_map_split(&maps->b, psi_split, (unsigned long long)cells,
+                                             (unsigned long long)m_total)))
         return cudaErrorInvalidValue;
     return cudaSuccess;
 }

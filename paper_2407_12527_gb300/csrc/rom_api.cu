@@ -97,12 +97,13 @@ struct rom_ctx {
     int n_ctas3 = 0, nwarps3 = 1, n_tx = 1, n_ty = 1;
 
     // dense scattering operator (mode 0); tensor-core variant: split BF16 psi and A
-    DevBuf psi, src_ord, Amat, dtab, psi_hi, psi_lo, a_hi, a_lo, tc_err;
+    DevBuf psi, src_ord, Amat, dtab, psi_split, a_hi, a_lo, tc_err;
     bool pmat_dirty = true;
     romk::DenseTcMaps tc_maps;
-    const void *tc_map_ptrs[4] = {nullptr, nullptr, nullptr, nullptr};
+    const void *tc_map_ptrs[3] = {nullptr, nullptr, nullptr};
     long long tc_map_cells = 0, tc_map_mtot = 0;
     int tc_map_S = 0;
+    int tc_b_groups = 1;
 
     // iteration state
     int MOM = 1;  // 1 isotropic moments, 3 linear moments, 0 dense operator
@@ -485,8 +486,7 @@ romk::SweepArgs sweep_args(const rom_ctx *ctx)
     if (ctx->MOM == 0) {
         a.src = (const float *)ctx->src_ord.p;
         if (ctx->opt.dense_precision == 1) {
-            a.psi_hi = ctx->psi_hi.p;
-            a.psi_lo = ctx->psi_lo.p;
+            a.psi_split = (uint32_t *)ctx->psi_split.p;
         } else {
             a.psi = (float *)ctx->psi.p;
         }
@@ -580,17 +580,17 @@ int prepare_dense(rom_ctx *ctx)
                     romk::dense_tc_max_m());
     if ((rc = ensure(ctx, ctx->src_ord, (size_t)ctx->Mtot * cells * sizeof(float)))) return rc;
     if (tc) {
-        const size_t half = (size_t)ctx->Mtot * cells * 2;  // BF16
+        const size_t split = (size_t)ctx->Mtot * cells * 4;  // BF16 hi + lo
         const size_t ab = (size_t)ctx->S * 128 * 128 * 2;
-        if ((rc = ensure(ctx, ctx->psi_hi, half)) || (rc = ensure(ctx, ctx->psi_lo, half)) ||
-            (rc = ensure(ctx, ctx->a_hi, ab)) || (rc = ensure(ctx, ctx->a_lo, ab)) ||
-            (rc = ensure(ctx, ctx->tc_err, sizeof(int))))
+        if ((rc = ensure(ctx, ctx->psi_split, split)) || (rc = ensure(ctx, ctx->a_hi, ab)) ||
+            (rc = ensure(ctx, ctx->a_lo, ab)) || (rc = ensure(ctx, ctx->tc_err, sizeof(int))))
             return rc;
-        const void *ptrs[4] = {ctx->a_hi.p, ctx->a_lo.p, ctx->psi_hi.p, ctx->psi_lo.p};
+        const void *ptrs[3] = {ctx->a_hi.p, ctx->a_lo.p, ctx->psi_split.p};
         if (memcmp(ptrs, ctx->tc_map_ptrs, sizeof ptrs) != 0 || ctx->tc_map_cells != cells ||
             ctx->tc_map_mtot != ctx->Mtot || ctx->tc_map_S != ctx->S) {
             CK(romk::make_dense_tc_maps(&ctx->tc_maps, ctx->a_hi.p, ctx->a_lo.p, ctx->S,
-                                        ctx->psi_hi.p, ctx->psi_lo.p, ctx->Mtot, cells));
+                                        ctx->psi_split.p, ctx->Mtot, cells,
+                                        &ctx->tc_b_groups));
             memcpy(ctx->tc_map_ptrs, ptrs, sizeof ptrs);
             ctx->tc_map_cells = cells;
             ctx->tc_map_mtot = ctx->Mtot;
@@ -702,6 +702,7 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
             ta.src = d.src;
             ta.active = d.active;
             ta.err = (int *)ctx->tc_err.p;
+            ta.b_groups_per_box = ctx->tc_b_groups;
             CK(romk::launch_dense_tc(ctx->tc_maps, ta, ctx->sm_count, st));
         } else {
             CK(romk::launch_dense_source(dense_args(ctx), max_m(ctx), st));
@@ -868,7 +869,7 @@ void rom_destroy(rom_ctx *ctx)
                       &ctx->active, &ctx->iters, &ctx->flags, &ctx->resid, &ctx->n_active,
                       &ctx->avg, &ctx->sum, &ctx->tmp, &ctx->psi, &ctx->src_ord, &ctx->Amat,
                       &ctx->dtab, &ctx->z32, &ctx->cta_begin_dev, &ctx->cta_list_dev,
-                      &ctx->xface, &ctx->yface, &ctx->err3, &ctx->psi_hi, &ctx->psi_lo,
+                      &ctx->xface, &ctx->yface, &ctx->err3, &ctx->psi_split,
                       &ctx->a_hi, &ctx->a_lo, &ctx->tc_err};
     for (DevBuf *b : bufs) release(*b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);

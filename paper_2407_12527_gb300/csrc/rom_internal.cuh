@@ -43,8 +43,8 @@ struct SweepArgs {
     const float *src;           // [S][MOM][J][NXP]; dense mode: [M_total][J][NXP] per ordinate
     float *part;                // [items][MOM][J][NXP] (dense mode: one moment, phi)
     float *psi;                 // dense mode: psi of every ordinate [M_total][J][NXP]
-    void *psi_hi, *psi_lo;      // dense mode, tensor cores: psi as BF16 hi / lo parts
-                                // [M_total][J][NXP] (psi unused when set)
+    uint32_t *psi_split;        // dense mode, tensor cores: psi as BF16 hi / lo parts,
+                                // [M_total][J * NXP / 8][hi 8 | lo 8] (psi unused when set)
     const SweepItem *items;
     const float *oc, *os, *ow;  // ordinate c, s, w
     const float *inflow;        // nullptr = vacuum; else face values [x_L:J][x_R:J][y_B:I][y_T:I]
@@ -145,9 +145,9 @@ struct DenseArgs {
 };
 
 // Dense source on the tensor cores (split BF16, tcgen05): TMA maps of A_hi,
-// A_lo [S][128][128] and Psi_hi, Psi_lo [M_total][cells] (BF16).
+// A_lo [S][128][128] and of the split psi [M_total][cells / 8][2][8] (BF16).
 struct DenseTcMaps {
-    CUtensorMap a_hi, a_lo, b_hi, b_lo;
+    CUtensorMap a_hi, a_lo, b;
 };
 struct DenseTcArgs {
     int S;
@@ -158,11 +158,12 @@ struct DenseTcArgs {
     float *src;                 // [M_total][cells]
     const int *active;
     int *err;                   // bits 2..7: a wait timed out
+    int b_groups_per_box;       // 8-cell groups per psi box of the map (16 or 1)
 };
 int dense_tc_max_m();
 cudaError_t make_dense_tc_maps(DenseTcMaps *maps, const void *a_hi, const void *a_lo, int S,
-                               const void *psi_hi, const void *psi_lo, long long m_total,
-                               long long cells);
+                               const void *psi_split, long long m_total, long long cells,
+                               int *b_groups_per_box);
 cudaError_t launch_dense_tc(const DenseTcMaps &maps, const DenseTcArgs &a, int n_ctas,
                             cudaStream_t st);
 cudaError_t launch_pmat_split(const float *A, const int *M, const long long *a_off, int S,

@@ -87,23 +87,29 @@ __device__ __forceinline__ float2 shfl1(float2 v)
 
 __device__ __forceinline__ void ld8(const float *__restrict__ p, float (&v)[kCols]) { ldg8_early(p, v); }
 __device__ __forceinline__ void st8(float *__restrict__ p, const float (&v)[kCols]) { stg8(p, v); }
-// psi of 8 cells as BF16 hi = bf16(v) and lo = bf16(v - hi), 16 bytes each
-__device__ __forceinline__ void st8_split(void *hi, void *lo, long long off, const float (&v)[kCols])
+// psi of 8 cells as BF16 parts in one 32-byte sector, [8 hi | 8 lo] (the byte
+// layout of the FP32 array): hi = v rounded to the nearest BF16 on its bit
+// pattern (add half a BF16 unit, clear the low 16 bits; ties away from zero;
+// two packed by one byte permute), lo = bf16_rn(v - hi) (the difference is exact
+// in FP32; two converted by one packed conversion).  hi + lo carries 16
+// significant bits of v, and lo has either sign, so the lo * lo term the
+// product drops has no bias.
+__device__ __forceinline__ void st8_split(uint32_t *psi2, long long off, const float (&v)[kCols])
 {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]);
-        const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * e + 1]);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
-        h[e] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        l[e] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        const uint32_t b0 = (__float_as_uint(v[2 * e]) + 0x8000u) & 0xFFFF0000u;
+        const uint32_t b1 = (__float_as_uint(v[2 * e + 1]) + 0x8000u) & 0xFFFF0000u;
+        h[e] = __byte_perm(b0, b1, 0x7632);
+        const float r0 = v[2 * e] - __uint_as_float(b0);
+        const float r1 = v[2 * e + 1] - __uint_as_float(b1);
+        const __nv_bfloat162 lo2 = __floats2bfloat162_rn(r0, r1);
+        l[e] = *reinterpret_cast<const uint32_t *>(&lo2);
     }
-    uint4 *ph = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(hi) + off);
-    uint4 *pl = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(lo) + off);
-    *ph = make_uint4(h[0], h[1], h[2], h[3]);
-    *pl = make_uint4(l[0], l[1], l[2], l[3]);
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(psi2 + off), "r"(h[0]),
+                 "r"(h[1]), "r"(h[2]), "r"(h[3]), "r"(l[0]), "r"(l[1]), "r"(l[2]), "r"(l[3])
+                 : "memory");
 }
 
 // Per-ordinate constants of a work item, grouped in packs.
@@ -294,7 +300,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &A, int blk, bool yn
 #pragma unroll
                 for (int k = 0; k < G; ++k) {
                     const long long off = (long long)o.ord[k] * A.cells + ra.base + h * ra.rs;
-                    if (A.psi_hi) st8_split(A.psi_hi, A.psi_lo, off, psi_row[k]);
+                    if (A.psi_split) st8_split(A.psi_split, off, psi_row[k]);
                     else st8(A.psi + off, psi_row[k]);
                 }
             }

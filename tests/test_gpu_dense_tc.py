@@ -1,0 +1,131 @@
+"""GPU parity of the tensor-core dense scattering source (dense_precision = 1).
+
+The dense operator's product D = A Psi runs on the tcgen05 tensor cores in
+split BF16 (A_hi Psi_hi + A_hi Psi_lo + A_lo Psi_hi, FP32 accumulation).  The
+bar is the one of every other GPU parity test: relative l2 difference of each
+sample's scalar flux <= 1e-5 against the FP64 oracle.  The cases cover uneven M
+per sample (sample row offsets that are not multiples of the 128-row operand
+tile, zero-padded operator columns), grids whose cell count is not a multiple
+of the 128-cell tile, full 128 x 128 operators, samples that stop iterating at
+different sweeps, and the FP32 CUDA-core path as a second reference.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+import rom_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rom():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2407_12527_gb300 import rom as R
+    return R
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def gpu_solve(R, I, J, bounds, st, ss, q, seed, nz, nt, kernel="hg", g=0.8, flags=0, **opts):
+    ctx = R.RomContext(0)
+    ctx.set_grid(I, J, bounds, st, ss, q)
+    ctx.set_ordinates_seed(seed, nz, nt)
+    ctx.set_kernel(kernel, g, flags)
+    ctx.set_options(**opts)
+    st_ = ctx.solve()
+    phi = np.stack([ctx.scalar_flux(k) for k in range(ctx.n_samples)])
+    it, _ = ctx.iterations()
+    ctx.close()
+    return {"phi": phi, "iters": it, "stats": st_}
+
+
+@pytest.mark.parametrize("flags", [0, 1, 2])
+def test_tc_hg_parity_uneven_m(rom, flags):
+    """M = 20, 16, 48 per sample on a 53 x 41 grid (2120 cells: 16 full tiles and a
+    ragged one); flags 1 = row-normalised operator, 2 = raw hemisphere kernel."""
+    I, J = 53, 41
+    bounds = (0.0, 1.0, 0.0, 0.8)
+    st, ss, q = W.random_medium(I, J, seed=71, ratio_max=0.8)
+    nz, nt = [1, 2, 2], [5, 2, 6]
+    gpu = gpu_solve(rom, I, J, bounds, st, ss, q, 73, nz, nt, flags=flags, fixed_iters=5,
+                    dense_precision=1)
+    sets = [O.rom_ordinates_xy(73, k, nz[k], nt[k]) for k in range(3)]
+    ref = O.solve_xy(I, J, bounds, st, ss, q, sets, kernel="hg", g=0.8, fixed_iters=5,
+                     normalize_rows=bool(flags & 1), raw=bool(flags & 2))
+    for k in range(3):
+        assert rel(gpu["phi"][k], ref["phi"][k]) < TOL, k
+
+
+def test_tc_hg_full_tiles(rom):
+    """M = 128 per sample (full 128 x 128 operator), 96 x 96 disc problem."""
+    p = W.hg_disc(n=96, n_samples=2)
+    nz, nt = [4, 4], [8, 8]
+    seed = W.ordinate_seed(3)
+    gpu = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, seed, nz, nt,
+                    fixed_iters=4, dense_precision=1)
+    sets = [O.rom_ordinates_xy(seed, k, 4, 8) for k in range(2)]
+    ref = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, sets, kernel="hg", g=0.8,
+                     fixed_iters=4)
+    for k in range(2):
+        assert rel(gpu["phi"][k], ref["phi"][k]) < TOL, k
+
+
+def test_tc_equals_fp32_product(rom):
+    """Split BF16 on the tensor cores against the FP32 CUDA-core product, same inputs."""
+    I, J = 64, 40
+    st, ss, q = W.random_medium(I, J, seed=3, ratio_max=0.9)
+    nz, nt = [2, 4, 3], [4, 8, 3]
+    kw = dict(fixed_iters=6)
+    a = gpu_solve(rom, I, J, (0, 1, 0, 1), st, ss, q, 17, nz, nt, dense_precision=0, **kw)
+    b = gpu_solve(rom, I, J, (0, 1, 0, 1), st, ss, q, 17, nz, nt, dense_precision=1, **kw)
+    for k in range(3):
+        assert rel(b["phi"][k], a["phi"][k]) < TOL, k
+
+
+def test_tc_converged_samples_leave_at_different_sweeps(rom):
+    """Converged solve: samples with different M stop at different sweeps, so later
+    launches skip the units of finished samples.  Row-normalised operator, so that
+    source iteration contracts for every M (an unnormalised Henyey-Greenstein
+    operator with few ordinates can have row sums above 1)."""
+    I, J = 48, 48
+    st, ss, q = W.random_medium(I, J, seed=9, ratio_max=0.9)
+    nz, nt = [1, 2, 4, 1], [2, 3, 8, 8]
+    gpu = gpu_solve(rom, I, J, (0, 1, 0, 1), st, ss, q, 29, nz, nt, flags=1, tol=1e-6,
+                    max_iter=400, dense_precision=1)
+    sets = [O.rom_ordinates_xy(29, k, nz[k], nt[k]) for k in range(4)]
+    ref = O.solve_xy(I, J, (0, 1, 0, 1), st, ss, q, sets, kernel="hg", g=0.8, tol=1e-12,
+                     max_iter=4000, normalize_rows=True)
+    for k in range(4):
+        assert rel(gpu["phi"][k], ref["phi"][k]) < 2e-5, k
+    assert len(set(int(x) for x in gpu["iters"])) > 1
+
+
+def test_tc_isotropic_dense_equals_moments(rom):
+    p = W.example_2_1(I=40, J=36)
+    kw = dict(fixed_iters=6)
+    a = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, 5, [2, 1], [2, 3],
+                  kernel="iso", g=0.0, **kw)
+    b = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, 5, [2, 1], [2, 3],
+                  kernel="iso", g=0.0, dense_source=1, dense_precision=1, **kw)
+    for k in range(2):
+        assert rel(b["phi"][k], a["phi"][k]) < TOL, k
+
+
+def test_tc_rejects_more_than_128_ordinates(rom):
+    ctx = rom.RomContext(0)
+    ctx.set_grid(8, 8, (0, 1, 0, 1), 1.0, 0.5, 1.0)
+    ctx.set_ordinates_seed(1, [4], [9])  # M = 144
+    ctx.set_kernel("hg", 0.5)
+    ctx.set_options(fixed_iters=1, dense_precision=1)
+    with pytest.raises(rom.RomError) as e:
+        ctx.solve()
+    assert e.value.code == -7
+    ctx.close()
