@@ -101,7 +101,8 @@ typedef struct rom_options {
                      /* BF16 on the tensor cores (tcgen05: A_hi Psi_hi + A_hi Psi_lo +     */
                      /* A_lo Psi_hi, FP32 accumulate, v_hi = v rounded to BF16, v_lo =     */
                      /* bf16(v - v_hi); psi kept as BF16 hi/lo, the bytes of FP32; at most */
-                     /* 128 ordinates per sample, else ROM_ERR_UNSUPPORTED)                */
+                     /* 128 ordinates per sample and 2048 samples per context, else        */
+                     /* ROM_ERR_UNSUPPORTED)                                               */
 } rom_options;
 
 /* Statistics of the last rom_solve. */

@@ -9,23 +9,23 @@
 // Precision: split BF16.  Each FP32 value v is carried as v_hi = v rounded to
 // the nearest BF16 (ties away from zero) and v_lo = bf16_rn(v - v_hi) (16
 // significant bits in all), written that way by the sweep (psi, as one 32-byte
-// sector [8 hi | 8 lo] per 8 cells) and by pmat_split_kernel (A), and
-//   D = A_hi Psi_hi + A_hi Psi_lo + A_lo Psi_hi
-// is accumulated in FP32 in tensor memory; the dropped A_lo Psi_lo term is
-// below 2^-18 of each product and of either sign.
+// sector [8 hi | 8 lo] per 8 cells) and by pmat_split_kernel (A).  Read as one
+// BF16 matrix, a row of psi is B' = [Psi_hi | Psi_lo] interleaved by 8 cells,
+// twice as wide; the tensor cores compute A_hi B' + A_lo B' (FP32 accumulate in
+// tensor memory, N = 256 per 128 cells) and the epilogue adds the hi and lo
+// columns of each cell: D = (A_hi + A_lo)(Psi_hi + Psi_lo).
 //
-// GB300 mapping: one persistent CTA per SM walks a contiguous range of
-// (sample, 128-cell tile) units.  Warp 0 (one lane) is the TMA producer: the
-// sample's A_hi / A_lo (K-major, two 64-column boxes each) once per sample and,
-// per unit, the Psi_hi / Psi_lo tile into a two-stage ring.  A is loaded with
-// the 128-byte swizzle; Psi, stored by the sweep as [row][8-cell group][hi | lo]
-// sectors, is loaded one 8-cell group x 128 rows box at a time (a 4D map over
-// [row][group][part][8], no swizzle), which lands as one column of 8 x 8 core
-// matrices of the canonical MN-major layout.  Warp 1 owns the
-// tensor memory (two 128 x 128 FP32 accumulators) and one lane issues, per
-// unit, 8 K-steps x 3 tcgen05.mma (kind::f16, BF16 in, FP32 accumulate, M = N =
-// 128), committing to mbarriers that free the Psi stage and hand the
-// accumulator to the epilogue.  Warps 2-5 read the accumulator (tcgen05.ld,
+// GB300 mapping: one persistent CTA per SM walks a contiguous range of the
+// (sample, 128-cell tile) units of the samples still iterating (every CTA
+// lists those samples the same way, so the work stays balanced as samples
+// finish).  Warp 0 (one lane) is the TMA producer: the sample's A_hi / A_lo
+// (K-major, two 64-column boxes each) once per sample and, per unit, the
+// 128 x 256 B' tile (MN-major, four 64-column boxes) into a two-stage ring, all
+// with the 128-byte swizzle.  Warp 1 owns the tensor memory (two 128 x 256 FP32
+// accumulators, all 512 columns) and one lane issues, per unit, 8 K-steps x 2
+// tcgen05.mma (kind::f16, BF16 in, FP32 accumulate, M = 128, N = 256),
+// committing to mbarriers that free the B' stage and hand the accumulator to
+// the epilogue.  Warps 2-5 read the accumulator (tcgen05.ld,
 // one TMEM lane per ordinate row), apply sigma_S and q (staged in shared memory
 // one unit ahead) and store the FP32 sources.  Every mbarrier wait is bounded;
 // on timeout the CTA raises an error flag, drains what it has in flight, frees
@@ -40,14 +40,16 @@ namespace romk {
 namespace {
 
 constexpr int kTileN = 128;                  // cells per unit
+constexpr int kMmaN = 2 * kTileN;            // B' columns per unit (hi and lo of each cell)
 constexpr int kK = 128;                      // ordinates (rows of A, K of the product)
 constexpr int kStages = 2;                   // Psi tile ring
 constexpr uint32_t kBox = 128 * 64 * 2;      // bytes of one 64-wide, 128-high bf16 box (16 KB)
 constexpr uint32_t kAbytes = 4 * kBox;       // A_hi + A_lo, two K-halves each (64 KB)
-constexpr uint32_t kBbytes = 4 * kBox;       // Psi_hi + Psi_lo, two cell-halves each (64 KB)
+constexpr uint32_t kBbytes = 4 * kBox;       // B' = [Psi_hi | Psi_lo], four 64-column boxes (64 KB)
 constexpr int kThreads = 6 * 32;
-constexpr uint32_t kTmemCols = 256;          // two accumulators of 128 columns
+constexpr uint32_t kTmemCols = 512;          // two accumulators of 256 columns
 constexpr unsigned kWaitTries = 1u << 22;
+constexpr int kMaxSamples = 2048;            // samples a launch can list (DenseTcArgs::S)
 
 struct TcBarriers {
     unsigned long long a_full, a_empty;
@@ -56,10 +58,12 @@ struct TcBarriers {
     uint32_t tmem_base;
     int abort_flag;
     float sq[2][2][kTileN];  // sigma_S and q of a unit's cells, per accumulator buffer
+    int n_act;               // samples still iterating, and their indices in order
+    int act[kMaxSamples];
 };
 // dynamic shared memory: [align pad][A 64 KB][B stage 0 64 KB][B stage 1 64 KB][barriers]
-constexpr uint32_t kSmemBytes = 1024 + kAbytes + kStages * kBbytes + 4096;
-static_assert(sizeof(TcBarriers) <= 4096, "barrier block");
+constexpr uint32_t kSmemBytes = 1024 + kAbytes + kStages * kBbytes + 12288;
+static_assert(sizeof(TcBarriers) <= 12288, "barrier block");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -120,16 +124,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
-                                            int c2, int c3, unsigned long long *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
-        "{%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
-        "r"(smem_u32(bar))
-        : "memory");
-}
 
 // Shared-memory matrix descriptor of tcgen05: start address, leading and stride
 // byte offsets (16-byte units), descriptor version 1, layout (bits 61-63: 0 no
@@ -143,9 +137,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 
 // Instruction descriptor, kind::f16: D FP32 (bits 4-5), A and B BF16 (bits 7-9,
 // 10-12), A K-major (bit 15 clear), B MN-major (bit 16), N >> 3 (bits 17-22),
-// M >> 4 (bits 24-28); M = N = 128.
+// M >> 4 (bits 24-28); M = 128, N = 256.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (0u << 15) | (1u << 16) |
-                            ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kK >> 4) << 24);
+                            ((uint32_t)(kMmaN >> 3) << 17) | ((uint32_t)(kK >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc)
 {
@@ -208,8 +202,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (int)((a.cells + kTileN - 1) / kTileN);
-    const UnitRange R = unit_range((long long)a.S * n_tiles);
 
+    if (warp == 2) {  // the samples still iterating, in order (the same list in every CTA)
+        int n = 0;
+        for (int s0 = 0; s0 < a.S; s0 += 32) {
+            const bool on = s0 + lane < a.S && a.active[s0 + lane] != 0;
+            const unsigned m = __ballot_sync(0xffffffffu, on);
+            if (on) bar->act[n + __popc(m & ((1u << lane) - 1u))] = s0 + lane;
+            n += __popc(m);
+        }
+        if (lane == 0) bar->n_act = n;
+    }
     if (threadIdx.x == 0) {
         mbar_init(&bar->a_full, 1);
         mbar_init(&bar->a_empty, 1);
@@ -235,18 +238,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = bar->tmem_base;
-
-    // the units a CTA computes: those of samples still iterating
-    auto active_unit = [&](long long u) { return a.active[(int)(u / n_tiles)] != 0; };
+    // units u = k * n_tiles + tile over the k-th sample still iterating
+    const UnitRange R = unit_range((long long)bar->n_act * n_tiles);
+    const int *act = bar->act;
 
     if (warp == 0) {
         if (lane == 0) {  // ---------------------------------------------- TMA producer
             int prev_s = -1, n_a = 0;
             long long n_b = 0;
             for (long long u = R.u0; u < R.u1; ++u) {
-                if (!active_unit(u)) continue;
                 if (*(volatile int *)&bar->abort_flag) break;
-                const int s = (int)(u / n_tiles), tile = (int)(u % n_tiles);
+                const int s = act[u / n_tiles], tile = (int)(u % n_tiles);
                 if (s != prev_s) {
                     if (n_a > 0 && !wait1(&bar->a_empty, (uint32_t)(n_a - 1) & 1u)) {
                         atomicOr(a.err, 4);
@@ -272,17 +274,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_expect_tx(&bar->b_full[st], kBbytes);
                 const uint32_t dst = sB + st * kBbytes;
                 const int row0 = (int)a.ord_off[s], x0 = tile * kTileN;
-                // part p (hi, lo) of group j: 128 rows x 16 B at dst + p * 32 KB + j * 2 KB
-                if (a.b_groups_per_box == kTileN / 8) {  // map with dims (e, row, part, group)
-                    for (int part = 0; part < 2; ++part)
-                        tma_load_4d(dst + part * 2 * kBox, &maps.b, 0, row0, part, x0 / 8,
-                                    &bar->b_full[st]);
-                } else {  // map with dims (e, part, group, row): one group per box
-                    for (int part = 0; part < 2; ++part)
-                        for (int j = 0; j < kTileN / 8; ++j)
-                            tma_load_4d(dst + part * 2 * kBox + j * 2048, &maps.b, 0, part,
-                                        x0 / 8 + j, row0, &bar->b_full[st]);
-                }
+                // B' columns [2 x0, 2 x0 + 256) of the rows of sample s: four 64-wide boxes
+                for (int nb = 0; nb < 4; ++nb)
+                    tma_load_2d(dst + nb * kBox, &maps.b, 2 * x0 + 64 * nb, row0, &bar->b_full[st]);
                 ++n_b;
             }
             // drain: the copies in flight complete before the CTA may leave
@@ -295,9 +289,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             int prev_s = -1, n_a = 0;
             long long n_b = 0;
             for (long long u = R.u0; u < R.u1; ++u) {
-                if (!active_unit(u)) continue;
                 if (*(volatile int *)&bar->abort_flag) break;
-                const int s = (int)(u / n_tiles);
+                const int s = act[u / n_tiles];
                 if (s != prev_s) {
                     if (!wait1(&bar->a_full, (uint32_t)n_a & 1u)) {
                         atomicOr(a.err, 16);
@@ -319,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t d = tmem + (uint32_t)acc * kTileN;
+                const uint32_t d = tmem + (uint32_t)acc * kMmaN;
                 const uint32_t bb = sB + st * kBbytes;
 #pragma unroll
                 for (int ks = 0; ks < kK / 16; ++ks) {
@@ -327,20 +320,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t aoff = (ks >> 2) * kBox + (ks & 3) * 32;
                     const uint64_t a_hi = smem_desc(sA + aoff, 16, 1024, 2);
                     const uint64_t a_lo = smem_desc(sA + 2 * kBox + aoff, 16, 1024, 2);
-                    // B: MN-major, no swizzle: 8 x 8 core matrices of 128 B, the next one
-                    // along K at +128 B (LBO), along the cells at +2 KB (SBO)
-                    const uint64_t b_hi = smem_desc(bb + ks * 256, 128, 2048, 0);
-                    const uint64_t b_lo = smem_desc(bb + 2 * kBox + ks * 256, 128, 2048, 0);
-                    mma_bf16(d, a_hi, b_hi, ks > 0 ? 1u : 0u);
-                    mma_bf16(d, a_hi, b_lo, 1u);
-                    mma_bf16(d, a_lo, b_hi, 1u);
+                    // B': MN-major, 8-row (k) atoms of 1024 B; the next 64 columns at +16 KB
+                    const uint64_t b = smem_desc(bb + ks * 2048, kBox, 1024, 2);
+                    mma_bf16(d, a_hi, b, ks > 0 ? 1u : 0u);
+                    mma_bf16(d, a_lo, b, 1u);
                 }
                 mma_commit(&bar->b_empty[st]);
                 mma_commit(&bar->acc_full[acc]);
                 // the last unit of this sample frees A for the producer
-                long long un = u + 1;
-                while (un < R.u1 && !active_unit(un)) ++un;
-                if (un >= R.u1 || (int)(un / n_tiles) != s) mma_commit(&bar->a_empty);
+                if (u + 1 >= R.u1 || act[(u + 1) / n_tiles] != s) mma_commit(&bar->a_empty);
                 ++n_b;
             }
             // the last products are complete before the tensor memory is freed
@@ -354,9 +342,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int row = 32 * g + lane;
         const int et = threadIdx.x - 64;  // 0..127
         long long n_b = 0;
-        // first active unit of the range, and the sigma_S / q value this thread stages
-        long long un = R.u0;
-        while (un < R.u1 && !active_unit(un)) ++un;
         auto fetch = [&](long long u, float &ssv, float &qv) {
             ssv = qv = 0.f;
             if (u < R.u1) {
@@ -368,17 +353,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         };
         float ss_next, q_next;
-        fetch(un, ss_next, q_next);
-        for (long long u = un; u < R.u1; ++u) {
-            if (!active_unit(u)) continue;
-            const int s = (int)(u / n_tiles), tile = (int)(u % n_tiles);
+        fetch(R.u0, ss_next, q_next);
+        for (long long u = R.u0; u < R.u1; ++u) {
+            const int s = act[u / n_tiles], tile = (int)(u % n_tiles);
             const int acc = (int)(n_b & 1);
             bar->sq[acc][0][et] = ss_next;
             bar->sq[acc][1][et] = q_next;
             asm volatile("bar.sync 1, 128;" ::: "memory");
-            long long u2 = u + 1;
-            while (u2 < R.u1 && !active_unit(u2)) ++u2;
-            fetch(u2, ss_next, q_next);
+            fetch(u + 1, ss_next, q_next);
             const bool ok = wait_warp(&bar->acc_full[acc], (uint32_t)(n_b >> 1) & 1u);
             // the four epilogue warps leave together or not at all (they share a named barrier)
             uint32_t any_fail;
@@ -397,21 +379,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             const long long n0 = (long long)tile * kTileN;
             float *dst = a.src + ((long long)a.ord_off[s] + row) * a.cells;
             const float *sss = bar->sq[acc][0], *sqq = bar->sq[acc][1];
+            // columns 16 j .. 16 j + 7: the hi products of cells 8 j .. 8 j + 7,
+            // columns 16 j + 8 .. 16 j + 15: their lo products
 #pragma unroll 1
-            for (int c = 0; c < kTileN / 32; ++c) {
+            for (int c = 0; c < kMmaN / 32; ++c) {
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)acc * kTileN + 32 * c, v);
-                const long long nc = n0 + 32 * c;
+                tmem_ld32(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)acc * kMmaN + 32 * c, v);
+                const long long nc = n0 + 16 * c;
                 if (row < M && nc < a.cells) {
 #pragma unroll
-                    for (int q8 = 0; q8 < 4; ++q8) {
+                    for (int q8 = 0; q8 < 2; ++q8) {
                         const long long n = nc + 8 * q8;
                         if (n < a.cells) {
                             float out[8];
 #pragma unroll
                             for (int e = 0; e < 8; ++e) {
-                                const int j = 32 * c + 8 * q8 + e;
-                                out[e] = fmaf(sss[j], v[8 * q8 + e], sqq[j]);
+                                const int j = 16 * c + 8 * q8 + e;
+                                out[e] = fmaf(sss[j], v[16 * q8 + e] + v[16 * q8 + 8 + e], sqq[j]);
                             }
                             stg8(dst + n, out);
                         }
@@ -472,39 +456,6 @@ EncodeFn encode_fn()
     return fn;
 }
 
-// 4D BF16 maps over the split psi [rows][cells / 8][2][8], no swizzle, zero fill
-// outside the tensor.  Preferred: dimensions listed as (element, row, part,
-// group), a box of 8 x 128 rows x 1 part x 16 groups landing as [group][row][8]
-// (16 core-matrix columns, 32 KB); returns 16 groups per box.  If the driver
-// refuses that order: dimensions (element, part, group, row), a box of one group
-// (128 rows x 16 bytes); returns 1.  0 on failure.
-int make_map_split(CUtensorMap *m, const void *ptr, unsigned long long cells,
-                   unsigned long long rows)
-{
-    EncodeFn fn = encode_fn();
-    if (!fn) return 0;
-    {
-        const cuuint64_t dims[4] = {8, rows, 2, cells / 8};
-        const cuuint64_t strides[3] = {cells * 4, 16, 32};
-        const cuuint32_t box[4] = {8, 128, 1, kTileN / 8};
-        const cuuint32_t estr[4] = {1, 1, 1, 1};
-        if (fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(ptr), dims, strides,
-               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
-            return kTileN / 8;
-    }
-    const cuuint64_t dims[4] = {8, 2, cells / 8, rows};
-    const cuuint64_t strides[3] = {16, 32, cells * 4};
-    const cuuint32_t box[4] = {8, 1, 1, 128};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(ptr), dims, strides, box,
-               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS
-               ? 1
-               : 0;
-}
-
 // 2D BF16 map over [rows][cols] (cols contiguous), 64 x 128 boxes, 128-byte swizzle,
 // zero fill outside the tensor.
 bool make_map(CUtensorMap *m, const void *ptr, unsigned long long cols, unsigned long long rows)
@@ -523,6 +474,7 @@ bool make_map(CUtensorMap *m, const void *ptr, unsigned long long cols, unsigned
 }  // namespace
 
 int dense_tc_max_m() { return kK; }
+int dense_tc_max_samples() { return kMaxSamples; }
 
 cudaError_t launch_pmat_split(const float *A, const int *M, const long long *a_off, int S,
                               void *hi, void *lo, cudaStream_t st)
@@ -533,8 +485,7 @@ cudaError_t launch_pmat_split(const float *A, const int *M, const long long *a_o
 }
 
 cudaError_t make_dense_tc_maps(DenseTcMaps *maps, const void *a_hi, const void *a_lo, int S,
-                               const void *psi_split, long long m_total, long long cells,
-                               int *b_groups_per_box)
+                               const void *psi_split, long long m_total, long long cells)
 {
     if ((cells % 8) != 0 || m_total < 1 || S < 1) return cudaErrorInvalidValue;
     // the kernel's shared memory (set on the current device, outside any capture)
@@ -544,8 +495,8 @@ cudaError_t make_dense_tc_maps(DenseTcMaps *maps, const void *a_hi, const void *
     if (e != cudaSuccess) return e;
     if (!make_map(&maps->a_hi, a_hi, kK, (unsigned long long)S * kK) ||
         !make_map(&maps->a_lo, a_lo, kK, (unsigned long long)S * kK) ||
-        !(*b_groups_per_box = make_map_split(&maps->b, psi_split, (unsigned long long)cells,
-                                             (unsigned long long)m_total)))
+        !make_map(&maps->b, psi_split, 2ull * (unsigned long long)cells,
+                  (unsigned long long)m_total))
         return cudaErrorInvalidValue;
     return cudaSuccess;
 }
@@ -554,6 +505,7 @@ cudaError_t launch_dense_tc(const DenseTcMaps &maps, const DenseTcArgs &a, int n
                             cudaStream_t st)
 {
     if (a.S <= 0 || n_ctas <= 0) return cudaSuccess;
+    if (a.S > kMaxSamples) return cudaErrorInvalidValue;
     dense_tc_kernel<<<n_ctas, kThreads, kSmemBytes, st>>>(maps, a);
     return cudaGetLastError();
 }

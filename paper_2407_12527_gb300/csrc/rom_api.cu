@@ -103,7 +103,6 @@ struct rom_ctx {
     const void *tc_map_ptrs[3] = {nullptr, nullptr, nullptr};
     long long tc_map_cells = 0, tc_map_mtot = 0;
     int tc_map_S = 0;
-    int tc_b_groups = 1;
 
     // iteration state
     int MOM = 1;  // 1 isotropic moments, 3 linear moments, 0 dense operator
@@ -578,6 +577,10 @@ int prepare_dense(rom_ctx *ctx)
         return fail(ctx, ROM_ERR_UNSUPPORTED,
                     "dense_precision = 1 (tensor cores) needs at most %d ordinates per sample",
                     romk::dense_tc_max_m());
+    if (tc && ctx->S > romk::dense_tc_max_samples())
+        return fail(ctx, ROM_ERR_UNSUPPORTED,
+                    "dense_precision = 1 (tensor cores) takes at most %d samples per context",
+                    romk::dense_tc_max_samples());
     if ((rc = ensure(ctx, ctx->src_ord, (size_t)ctx->Mtot * cells * sizeof(float)))) return rc;
     if (tc) {
         const size_t split = (size_t)ctx->Mtot * cells * 4;  // BF16 hi + lo
@@ -589,8 +592,7 @@ int prepare_dense(rom_ctx *ctx)
         if (memcmp(ptrs, ctx->tc_map_ptrs, sizeof ptrs) != 0 || ctx->tc_map_cells != cells ||
             ctx->tc_map_mtot != ctx->Mtot || ctx->tc_map_S != ctx->S) {
             CK(romk::make_dense_tc_maps(&ctx->tc_maps, ctx->a_hi.p, ctx->a_lo.p, ctx->S,
-                                        ctx->psi_split.p, ctx->Mtot, cells,
-                                        &ctx->tc_b_groups));
+                                        ctx->psi_split.p, ctx->Mtot, cells));
             memcpy(ctx->tc_map_ptrs, ptrs, sizeof ptrs);
             ctx->tc_map_cells = cells;
             ctx->tc_map_mtot = ctx->Mtot;
@@ -702,7 +704,6 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
             ta.src = d.src;
             ta.active = d.active;
             ta.err = (int *)ctx->tc_err.p;
-            ta.b_groups_per_box = ctx->tc_b_groups;
             CK(romk::launch_dense_tc(ctx->tc_maps, ta, ctx->sm_count, st));
         } else {
             CK(romk::launch_dense_source(dense_args(ctx), max_m(ctx), st));

@@ -145,7 +145,8 @@ struct DenseArgs {
 };
 
 // Dense source on the tensor cores (split BF16, tcgen05): TMA maps of A_hi,
-// A_lo [S][128][128] and of the split psi [M_total][cells / 8][2][8] (BF16).
+// A_lo [S][128][128] and of the split psi as one BF16 matrix [M_total][2 cells]
+// (rows of [8 hi | 8 lo] per 8 cells).
 struct DenseTcMaps {
     CUtensorMap a_hi, a_lo, b;
 };
@@ -158,12 +159,11 @@ struct DenseTcArgs {
     float *src;                 // [M_total][cells]
     const int *active;
     int *err;                   // bits 2..7: a wait timed out
-    int b_groups_per_box;       // 8-cell groups per psi box of the map (16 or 1)
 };
 int dense_tc_max_m();
+int dense_tc_max_samples();
 cudaError_t make_dense_tc_maps(DenseTcMaps *maps, const void *a_hi, const void *a_lo, int S,
-                               const void *psi_split, long long m_total, long long cells,
-                               int *b_groups_per_box);
+                               const void *psi_split, long long m_total, long long cells);
 cudaError_t launch_dense_tc(const DenseTcMaps &maps, const DenseTcArgs &a, int n_ctas,
                             cudaStream_t st);
 cudaError_t launch_pmat_split(const float *A, const int *M, const long long *a_off, int S,
