@@ -186,6 +186,25 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def traffic_record(name, source_file, samples_now):
+    """DRAM bytes of one full launch (every sample active) of a kernel, from the
+    committed ncu capture profiles/<name>.traffic.json, scaled from the captured
+    batch to samples_now samples; None when the kernel source differs from the
+    one captured (sha256) or no record exists."""
+    import hashlib
+    tpath = os.path.join(ROOT, "profiles", name + ".traffic.json")
+    spath = os.path.join(ROOT, "paper_2407_12527_gb300", "csrc", source_file)
+    if not os.path.exists(tpath):
+        return None
+    with open(tpath) as f:
+        tr = json.load(f)
+    with open(spath, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()
+    if tr.get("source_sha256") != digest:
+        return None
+    return tr["dram_bytes_per_launch"] * samples_now / tr["samples"]
+
+
 def measured_hbm_gbs():
     """Measured copy bandwidth of this GPU pool (MEASURED_PEAKS.json), else the
     fallback figure of an earlier GB300 measurement."""
@@ -442,23 +461,20 @@ def run_ours(args):
         achieved = sweep_upd * fpu / (sweep_ms / 1e3) / 1e12
         kernel_name = "sweep3d_kernel (K9)" if WL.dim == 3 else "sweep2d_kernel (K1)"
         kernel_name, n_l, avg_us, fu = (kernel_name, sweep_n, 1e3 * sweep_ms / max(sweep_n, 1), fpu)
-    # DRAM bytes of one full sweep launch from the committed ncu capture, used
-    # only while the sweep source is the one that was captured
+    # DRAM bytes of one full launch from the committed ncu captures, used only
+    # while the kernel source is the one that was captured
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "sweep2d_point_source_256x64.traffic.json")
-    spath = os.path.join(ROOT, "paper_2407_12527_gb300", "csrc", "sweep2d.cu")
-    if WL.name == "point_source" and os.path.exists(tpath) and s["tile_g"] == 2:
-        import hashlib
-        with open(tpath) as f:
-            tr = json.load(f)
-        with open(spath, "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()
-        if tr.get("sweep2d_cu_sha256") == digest:
-            traffic = tr.get("dram_bytes_per_launch")
+    if WL.name == "point_source" and s["tile_g"] == 2:
+        traffic = traffic_record("sweep2d_point_source_256", "sweep2d.cu", WL.samples)
+    elif WL.name == "lognormal_cube" and s["tile_g"] == 2:
+        traffic = traffic_record("sweep3d_lognormal_cube_128", "sweep3d.cu", WL.samples)
     if tc and src_ms > 0:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "traffic": None,
-                    "traffic_note": "algorithmic bytes: psi (BF16 hi + lo) read and FP32 sources "
+                    "frac": achieved / hbm_peak,
+                    "traffic": traffic_record("dense_tc_hg_disc_512", "dense_tc.cu", WL.samples),
+                    "traffic_note": "DRAM read+write bytes of one launch with every sample "
+                                    "active (ncu, scaled by samples); achieved counts the "
+                                    "algorithmic bytes, psi (BF16 hi + lo) read and FP32 sources "
                                     "written, 8 B per cell and ordinate",
                     "kernel": kernel_name, "launches": n_l, "avg_launch_us": avg_us,
                     "contraction_tflops": src_flop / (src_ms / 1e3) / 1e12,
@@ -469,7 +485,8 @@ def run_ours(args):
     if roofline is None:
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                    "traffic_note": "DRAM read+write bytes of one full sweep launch (ncu)",
+                    "traffic_note": "DRAM read+write bytes of one sweep launch with every "
+                                    "sample active (ncu, scaled by samples)",
                     "kernel": kernel_name, "launches": n_l, "avg_launch_us": avg_us,
                     "flop_per_update": fu,
                     "sweep_avg_launch_us": 1e3 * sweep_ms / max(sweep_n, 1),
@@ -644,6 +661,9 @@ def main():
     ap.add_argument("--dense-precision", type=int, default=1, choices=[0, 1],
                     help="dense scattering operator product: 0 FP32 CUDA cores, 1 split BF16 "
                          "on the tcgen05 tensor cores")
+    ap.add_argument("--samples", type=int, default=0,
+                    help="ROM samples per step (0: the workload's own count); smaller batches "
+                         "serve the small-case profiler captures")
     ap.add_argument("--only-timed", action="store_true",
                     help="run the warm-up and timed steps only (no roofline, e2e or CPU legs)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -669,6 +689,10 @@ def main():
     if args.rom_vs_dom:
         return run_rom_vs_dom(args)
     WL = make_workload(args.workload)
+    if args.samples > 0 and not WL.quad:
+        k = args.samples
+        WL.nz = [WL.nz[i % len(WL.nz)] for i in range(k)]
+        WL.nt = [WL.nt[i % len(WL.nt)] for i in range(k)]
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
