@@ -83,6 +83,11 @@ def lib() -> ctypes.CDLL:
             ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, ctypes.c_int, ip, dp, dp,
             dp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
             dp, ip, dp, dp]
+        L.oracle_solve_xy_linear_moments.restype = ctypes.c_int
+        L.oracle_solve_xy_linear_moments.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+            ctypes.c_double, dp, dp, dp, ctypes.c_int, ip, dp, dp, dp, ctypes.c_double,
+            ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ip, dp]
         L.oracle_max_threads.restype = ctypes.c_int
         L.oracle_max_threads.argtypes = []
         _lib = L
@@ -325,6 +330,33 @@ def solve_xyz(I, J, K, bounds, sigma_t, sigma_s, q, ordinate_sets, *, scheme="dd
     if rc not in (0, -4):
         raise ValueError(f"oracle_solve_xyz failed ({rc})")
     return {"phi": phi, "iters": iters, "resid": resid, "leak": leak}
+
+
+def solve_xy_linear_moments(I, J, bounds, sigma_t, sigma_s, q, ordinate_sets, g, *,
+                            scheme="dd", tol=1e-10, max_iter=10000, fixed_iters=0, n_threads=0,
+                            allow_not_converged=False):
+    """Linear kernel P = 1 + g cos(xi) (mirror-averaged, unnormalised) by its three
+    angular moments phi, Jx, Jy (eq. anisotropic kernel), vacuum inflow; for ordinate
+    sets too large for the dense operator of solve_xy.  Returns dict(phi, iters, resid)."""
+    st, ss, qq = (_f64(np.broadcast_to(a, (J, I))) for a in (sigma_t, sigma_s, q))
+    ns = len(ordinate_sets)
+    mps = np.array([o.M for o in ordinate_sets], dtype=np.int32)
+    cat = [_f64(np.concatenate([getattr(o, f) for o in ordinate_sets])) if ns else np.zeros(1)
+           for f in ("c", "s", "w")]
+    phi = np.zeros((ns, J, I))
+    iters = np.zeros(ns, dtype=np.int32)
+    resid = np.zeros(ns)
+    ip = ctypes.POINTER(ctypes.c_int)
+    rc = lib().oracle_solve_xy_linear_moments(
+        I, J, float(bounds[0]), float(bounds[1]), float(bounds[2]), float(bounds[3]), _dp(st),
+        _dp(ss), _dp(qq), ns, mps.ctypes.data_as(ip), *(_dp(a) for a in cat), float(g),
+        SCHEMES[scheme], float(tol), int(max_iter), int(fixed_iters), int(n_threads), _dp(phi),
+        iters.ctypes.data_as(ip), _dp(resid))
+    if rc == -4 and not allow_not_converged:
+        raise RuntimeError("oracle: source iteration did not converge")
+    if rc not in (0, -4):
+        raise ValueError(f"oracle_solve_xy_linear_moments failed ({rc})")
+    return {"phi": phi, "iters": iters, "resid": resid}
 
 
 def max_threads() -> int:

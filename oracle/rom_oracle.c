@@ -413,6 +413,98 @@ int oracle_solve_xy(int I, int J, double xl, double xr, double yb, double yt,
     return status;
 }
 
+/*
+ * Source iteration with the linear kernel P = 1 + g cos(xi) (eq. anisotropic
+ * kernel) in its mirror-averaged form 1 + g (cc' + ss'), carried by three
+ * angular moments instead of the dense operator: with phi = sum w psi,
+ * Jx = sum w c psi, Jy = sum w s psi of the previous sweep,
+ *   S_l = sigma_S (phi + g (c_l Jx + s_l Jy)) + q,
+ * which is sum_l' w_l' P(u_l', u_l) psi_l' written out.  Vacuum inflow;
+ * arguments as oracle_solve_xy.  Used for references with very many ordinates,
+ * where the M x M operator does not fit.
+ */
+int oracle_solve_xy_linear_moments(int I, int J, double xl, double xr, double yb, double yt,
+                                   const double *sigma_t, const double *sigma_s, const double *q,
+                                   int n_samples, const int *m_per_sample, const double *c,
+                                   const double *s, const double *w, double g, int scheme,
+                                   double tol, int max_iter, int fixed_iters, int n_threads,
+                                   double *phi_out, int *iters_out, double *resid_out)
+{
+    if (I < 1 || J < 1 || n_samples < 0 || !(xr > xl) || !(yt > yb)) return ORACLE_EINVAL;
+    if (scheme != SCHEME_DD && scheme != SCHEME_STEP) return ORACLE_EINVAL;
+    if (fixed_iters <= 0 && max_iter < 1) return ORACLE_EINVAL;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    const grid_t G = {I, J, (xr - xl) / I, (yt - yb) / J};
+    const size_t nc = (size_t)I * J;
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    int status = ORACLE_OK;
+    long offset = 0;
+    for (int smp = 0; smp < n_samples; ++smp) {
+        const int M = m_per_sample[smp];
+        const double *cs = c + offset, *ss = s + offset, *ws = w + offset;
+        double *phi = phi_out + (size_t)smp * nc;
+        double *jx = calloc(nc, sizeof(double)), *jy = calloc(nc, sizeof(double));
+        double *mom_new = calloc(3 * nc, sizeof(double));
+        double *part = calloc(3 * nc * (size_t)nthr, sizeof(double));
+        double *psi_tmp = malloc(nc * (size_t)nthr * sizeof(double));
+        double *src_tmp = malloc(nc * (size_t)nthr * sizeof(double));
+        double *psi_y = malloc((size_t)I * nthr * sizeof(double));
+        if (!jx || !jy || !mom_new || !part || !psi_tmp || !src_tmp || !psi_y) {
+            free(jx); free(jy); free(mom_new); free(part); free(psi_tmp); free(src_tmp); free(psi_y);
+            return ORACLE_ENOMEM;
+        }
+        memset(phi, 0, nc * sizeof(double));
+        int it = 0;
+        double resid = INFINITY;
+        const int limit = fixed_iters > 0 ? fixed_iters : max_iter;
+        while (it < limit) {
+            memset(part, 0, 3 * nc * (size_t)nthr * sizeof(double));
+#pragma omp parallel for schedule(static)
+            for (int l = 0; l < M; ++l) {
+                int t = 0;
+#ifdef _OPENMP
+                t = omp_get_thread_num();
+#endif
+                double *psi = psi_tmp + (size_t)t * nc, *src = src_tmp + (size_t)t * nc;
+                for (size_t k = 0; k < nc; ++k)
+                    src[k] = sigma_s[k] * (phi[k] + g * (cs[l] * jx[k] + ss[l] * jy[k])) + q[k];
+                sweep_ordinate(&G, sigma_t, src, cs[l], ss[l], scheme, NULL, psi,
+                               psi_y + (size_t)t * I);
+                double *pt = part + 3 * nc * (size_t)t;
+                for (size_t k = 0; k < nc; ++k) {
+                    pt[k] += ws[l] * psi[k];
+                    pt[nc + k] += ws[l] * cs[l] * psi[k];
+                    pt[2 * nc + k] += ws[l] * ss[l] * psi[k];
+                }
+            }
+            for (size_t k = 0; k < 3 * nc; ++k) {
+                double acc = 0.0;
+                for (int t = 0; t < nthr; ++t) acc += part[3 * nc * (size_t)t + k];
+                mom_new[k] = acc;
+            }
+            resid = l2diff_rel(mom_new, phi, nc);
+            memcpy(phi, mom_new, nc * sizeof(double));
+            memcpy(jx, mom_new + nc, nc * sizeof(double));
+            memcpy(jy, mom_new + 2 * nc, nc * sizeof(double));
+            ++it;
+            if (fixed_iters <= 0 && resid < tol) break;
+        }
+        if (fixed_iters <= 0 && !(resid < tol)) status = ORACLE_ENOTCONV;
+        if (iters_out) iters_out[smp] = it;
+        if (resid_out) resid_out[smp] = resid;
+        free(jx); free(jy); free(mom_new); free(part); free(psi_tmp); free(src_tmp); free(psi_y);
+        offset += M;
+    }
+    return status;
+}
+
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
 int oracle_max_threads(void)
 {

@@ -580,3 +580,22 @@ def test_3d_rom_set_mirror_symmetry_and_moments():
     vals = np.array([np.sum(q.w * q.zeta ** 2) for q in
                      (O.rom_ordinates_xyz(5, k, 1, 2) for k in range(2000))])
     assert abs(vals.mean() - 1 / 3) < 5 * vals.std() / np.sqrt(vals.size)
+
+
+@pytest.mark.parametrize("scheme", ["dd", "step"])
+def test_linear_moment_form_equals_dense_operator(scheme):
+    """The three-moment linear-kernel iteration equals the dense-operator one
+    (mirror-averaged kernel, unnormalised) sweep for sweep."""
+    I, J = 9, 7
+    rng = np.random.default_rng(41)
+    st = rng.uniform(0.5, 3.0, size=(J, I))
+    ss = st * rng.uniform(0, 0.8, size=(J, I))
+    q = rng.uniform(0, 2.0, size=(J, I))
+    sets = [O.rom_ordinates_xy(5, k, 2, 3) for k in range(2)] + [O.quad_gauss_xy(3)]
+    for kw in (dict(fixed_iters=4), dict(tol=1e-13)):
+        a = O.solve_xy_linear_moments(I, J, (0, 1, 0, 0.7), st, ss, q, sets, 0.9, scheme=scheme,
+                                      **kw)
+        b = O.solve_xy(I, J, (0, 1, 0, 0.7), st, ss, q, sets, kernel="linear", g=0.9,
+                       scheme=scheme, **kw)
+        np.testing.assert_allclose(a["phi"], b["phi"], rtol=1e-12, atol=1e-14)
+        assert list(a["iters"]) == list(b["iters"])
