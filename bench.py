@@ -645,6 +645,90 @@ def run_rom_vs_dom(args):
     return 0
 
 
+# ------------------------------------------------- Example 2.1 experiment tables
+
+# Values the paper prints for Example 2.1 (Sec. 4.2): error E and bias B of ROM with
+# t = 10240 samples, Delta S = pi/64, pi/36, pi/16, pi/4, and the ray-effect measure
+# e_inf of DOM with 36 and 144 ordinates and of ROM with 16 samples of 36 ordinates.
+PAPER_E8 = {
+    "E": {"0.0": [8.09e-3, 1.25e-2, 2.26e-2, 6.28e-2], "0.9": [8.18e-3, 1.26e-2, 2.28e-2, 6.36e-2]},
+    "B": {"0.0": [1.12e-4, 2.62e-4, 6.44e-4, 6.22e-3], "0.9": [1.09e-4, 2.01e-4, 3.95e-4, 5.42e-3]},
+    "order_E": {"0.0": 0.74, "0.9": 0.74}, "order_B": {"0.0": 1.44, "0.9": 1.41},
+}
+PAPER_E10 = {"dom_36": 0.0373, "dom_144": 0.0206, "rom_16x36": 0.012}
+
+
+def run_paper_tables(args):
+    """Example 2.1 at the paper's scale on the GPU: ROM error E (mean over samples of
+    the l2 error of one sample) and bias B (l2 error of the sample average), eq.
+    (l2norm2D), for t samples at Delta S = pi/(4 N^2), N = 4, 3, 2, 1, kernels g = 0
+    and g = 0.9; e_inf for DOM (uniform N = 3, 6) and ROM (16 samples of N = 3).
+    Reference: the FP64 oracle with the Gaussian set N = args.ref_n (2 N (N + 1)
+    ordinates; the linear kernel through its three moments), SI to 1e-10."""
+    from oracle import oracle as O
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2407_12527_gb300 import RomContext
+
+    t = args.table_samples
+    batch = args.table_batch
+    out = {"metric": f"ROM error and bias on Example 2.1 (100x100, t = {t} samples) and the "
+                     f"ray-effect measure, 1 GB300", "data": "synthetic",
+           "reference": f"FP64 oracle, 2D Gaussian set N={args.ref_n}, SI to 1e-10",
+           "paper": {"table_t10240": PAPER_E8, "e_inf": PAPER_E10}, "ours": {}}
+    for g in (0.0, 0.9):
+        p = W.example_2_1(g=g)
+        ref_set = O.quad_gauss_xy(args.ref_n)
+        t0 = time.perf_counter()
+        if g == 0.0:
+            ref = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, [ref_set],
+                             tol=1e-10)["phi"][0]
+        else:
+            ref = O.solve_xy_linear_moments(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q,
+                                            [ref_set], g, tol=1e-10)["phi"][0]
+        ref_s = time.perf_counter() - t0
+        ctx = RomContext(0)
+        ctx.set_grid(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q)
+        if g:
+            ctx.set_kernel("linear", g)
+        ctx.set_options(tol=TOL)
+        rows = []
+        for N in (4, 3, 2, 1):
+            errs, acc, n, gpu_ms = [], np.zeros((p.J, p.I)), 0, 0.0
+            while n < t:
+                b = min(batch, t - n)
+                ctx.set_ordinates_seed(W.ordinate_seed(10, int(10 * g)), [N] * b, [N] * b,
+                                       first_sample=n)
+                st = ctx.solve()
+                gpu_ms += st["gpu_ms"]
+                errs.extend(O.l2_xy(ctx.scalar_flux(k), ref) for k in range(b))
+                part, cnt = ctx.partial_sum()
+                acc += part
+                n += cnt
+            rows.append({"delta_S": f"pi/{4 * N * N}", "M": 4 * N * N,
+                         "E": float(np.mean(errs)), "B": O.l2_xy(acc / n, ref),
+                         "gpu_ms": gpu_ms})
+        dS = np.log([np.pi / r["M"] for r in rows])  # Delta S = pi / (4 N^2) = pi / M
+        order_E = float(np.polyfit(dS, np.log([r["E"] for r in rows]), 1)[0])
+        order_B = float(np.polyfit(dS, np.log([r["B"] for r in rows]), 1)[0])
+        res = {"rows": rows, "order_E": order_E, "order_B": order_B,
+               "reference_host_s": ref_s}
+        if g == 0.0:  # ray-effect measure (the paper does not say which kernel: g = 0 assumed)
+            e = {}
+            for name, n_uni in (("dom_36", 3), ("dom_144", 6)):
+                ctx.set_quadrature("uniform", n_uni)
+                ctx.solve()
+                e[name] = O.e_inf(ctx.scalar_flux(-1), ref)
+            ctx.set_ordinates_seed(W.ordinate_seed(10, 5), [3] * 16, [3] * 16)
+            ctx.solve()
+            e["rom_16x36"] = O.e_inf(ctx.scalar_flux(-1), ref)
+            res["e_inf"] = e
+        ctx.close()
+        out["ours"][f"{g}"] = res
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -683,11 +767,17 @@ def main():
                     help="ordinate cells per quadrant (M = 4 m)")
     ap.add_argument("--rom-batch", type=int, default=256)
     ap.add_argument("--rom-max", type=int, default=4096)
+    ap.add_argument("--paper-tables", action="store_true",
+                    help="Example 2.1 ROM error / bias table and ray-effect measure (Sec. 4.2)")
+    ap.add_argument("--table-samples", type=int, default=10240)
+    ap.add_argument("--table-batch", type=int, default=1024)
     args = ap.parse_args()
     global WL, ARGS
     ARGS = args
     if args.rom_vs_dom:
         return run_rom_vs_dom(args)
+    if args.paper_tables:
+        return run_paper_tables(args)
     WL = make_workload(args.workload)
     if args.samples > 0 and not WL.quad:
         k = args.samples

@@ -599,3 +599,17 @@ def test_linear_moment_form_equals_dense_operator(scheme):
                        scheme=scheme, **kw)
         np.testing.assert_allclose(a["phi"], b["phi"], rtol=1e-12, atol=1e-14)
         assert list(a["iters"]) == list(b["iters"])
+
+
+def test_example21_ray_effect_measure_dom():
+    """e_inf of DOM with 36 and 144 ordinates against the 80400-ordinate Gaussian
+    reference (Sec. 4.2), to the printed 3 digits (tests/golden/example21_ray_effect.txt)."""
+    p = W.example_2_1()
+    ref = _solve(p, O.quad_gauss_xy(200), tol=1e-10)
+    with open(os.path.join(GOLDEN, "example21_ray_effect.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for quad, N, M, want in rows:
+        o = O.quad_uniform_xy(int(N))
+        assert o.M == int(M)
+        got = O.e_inf(_solve(p, o, tol=1e-10), ref)
+        assert abs(got - float(want)) <= 0.5e-4, (N, got, want)
