@@ -57,16 +57,16 @@ __global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
         ldg8(A.sigma_s + v, ss);
         ldg8(A.q + v, qq);
         int it = ib;
-        if (A.zero_part) {  // the sample's one accumulated array, cleared for the next sweep
-            float *p = const_cast<float *>(A.part) + (long long)ib * cells + v;
-            float t[8], zero[8];
-            ld8_volatile(p, t);
+        if (A.zero_part) {  // the sample's accumulated moments, cleared for the next sweep
+            float zero[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                acc[0][e] = t[e];
-                zero[e] = 0.f;
+            for (int e = 0; e < 8; ++e) zero[e] = 0.f;
+#pragma unroll
+            for (int m = 0; m < MOM; ++m) {
+                float *p = const_cast<float *>(A.part) + ((long long)s * MOM + m) * cells + v;
+                ld8_volatile(p, acc[m]);
+                stg8(p, zero);
             }
-            stg8(p, zero);
             it = ie;
         }
         // items in batches of eight independent loads, summed in item order

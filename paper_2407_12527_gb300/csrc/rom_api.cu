@@ -256,6 +256,14 @@ int set_grid_common(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3
 }
 
 // 1: isotropic moment, 3: linear-kernel moments, 0: dense operator
+// The sweep adds each sample's moments to one accumulator (vector atomics; the
+// combine reads and clears it) instead of storing per-item partials that the
+// combine sums in item order: in 3D (per-item partials would be cells x
+// ordinates) and with the dense operator (many items per sample, partials of
+// GB size).  The moment modes in X-Y keep the per-item partials: few items per
+// sample, bitwise reproducible sums, and faster there.
+bool accumulates(const rom_ctx *ctx) { return ctx->dim == 3 || ctx->MOM == 0; }
+
 int source_mode(const rom_ctx *ctx)
 {
     if (ctx->opt.dense_source) return 0;
@@ -676,7 +684,7 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     romk::CombineArgs ca{};
     ca.S = ctx->S;
     ca.MOM = ctx->MOM == 0 ? 1 : ctx->MOM;
-    ca.zero_part = ctx->dim == 3 ? 1 : 0;
+    ca.zero_part = accumulates(ctx) ? 1 : 0;
     ca.chunks = ctx->chunks;
     ca.cells = padded_cells(ctx);
     ca.cells4 = ca.cells / 4;
@@ -742,7 +750,8 @@ int autotune_g(rom_ctx *ctx)
         if (G > cap) continue;
         ctx->opt.tile_g = G;
         if ((rc = build_items(ctx))) return rc;
-        if ((rc = ensure(ctx, ctx->part, ctx->items.size() * MOMk * cells * sizeof(float))))
+        const size_t units = accumulates(ctx) ? (size_t)ctx->S : ctx->items.size();
+        if ((rc = ensure(ctx, ctx->part, units * MOMk * cells * sizeof(float))))
             return rc;
         CK(romk::launch_init_state(ctx->S, MOMk, cells, (const float *)ctx->q.p,
                                    (float *)ctx->phi.p, (float *)ctx->src.p, (int *)ctx->active.p,
@@ -1340,8 +1349,8 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     const int MOM = ctx->MOM == 0 ? 1 : ctx->MOM;  // moments kept per sample
     const size_t state = (size_t)ctx->S * MOM * cells * sizeof(float);
     const size_t nI = (size_t)n_cells(ctx);
-    // part: per work item (2D), or the accumulated flux of each sample (3D)
-    const size_t part_units = ctx->dim == 3 ? (size_t)ctx->S : ctx->items.size();
+    // part: the moments of each sample accumulated by the sweep, or of each work item
+    const size_t part_units = accumulates(ctx) ? (size_t)ctx->S : ctx->items.size();
     void *before[] = {ctx->phi.p, ctx->src.p, ctx->part.p, ctx->partials.p, ctx->active.p};
     if ((rc = ensure(ctx, ctx->phi, state)) || (rc = ensure(ctx, ctx->src, state)) ||
         (rc = ensure(ctx, ctx->part, part_units * MOM * cells * sizeof(float))) ||
@@ -1363,7 +1372,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     if (ctx->dim == 2 && ctx->opt.tile_g == -1 && ctx->tuned_g == 0) {
         if ((rc = autotune_g(ctx))) return rc;
         if ((rc = build_items(ctx))) return rc;
-        if ((rc = ensure(ctx, ctx->part, ctx->items.size() * MOM * cells * sizeof(float))))
+        if ((rc = ensure(ctx, ctx->part, part_units * MOM * cells * sizeof(float))))
             return rc;
         invalidate_graph(ctx);
     }
@@ -1374,10 +1383,9 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     if (ctx->MOM == 0 && ctx->opt.dense_precision == 1)
         CK(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), ctx->stream));
-    if (ctx->dim == 3) {  // the sweep accumulates into part; the combine clears it
-        CK(cudaMemsetAsync(ctx->part.p, 0, part_units * cells * sizeof(float), ctx->stream));
-        CK(cudaMemsetAsync(ctx->err3.p, 0, sizeof(int), ctx->stream));
-    }
+    if (accumulates(ctx))  // the sweep accumulates into part; the combine clears it
+        CK(cudaMemsetAsync(ctx->part.p, 0, part_units * MOM * cells * sizeof(float), ctx->stream));
+    if (ctx->dim == 3) CK(cudaMemsetAsync(ctx->err3.p, 0, sizeof(int), ctx->stream));
     CK(romk::launch_init_state(ctx->S, MOM, cells, (const float *)ctx->q.p, (float *)ctx->phi.p,
                                (float *)ctx->src.p, (int *)ctx->active.p, (int *)ctx->iters.p,
                                (int *)ctx->flags.p, (double *)ctx->resid.p, ctx->stream));

@@ -6,7 +6,8 @@
 //   sigma_t, sigma_s, q      [J][NXP]
 //   phi    (per sample)      [S][MOM][J][NXP]   current iterate, MOM scalar moments
 //   src    (per sample)      [S][MOM][J][NXP]   source moments for the next sweep
-//   part   (per work item)   [items][MOM][J][NXP]  moments of one item's sweep
+//   part   (per work item)   [items][MOM][J][NXP]  moments of one item's sweep, or
+//          (per sample)      [S][MOM][J][NXP]      moments accumulated by the sweep
 //   ordinates                c, s, w [M_total] (FP32) and c, s, zeta, w (FP64)
 //   residual partials        [S][chunks][2] FP64
 // MOM = 1 for isotropic scattering (phi), 3 for the linear kernel (phi, Jx, Jy).
@@ -52,10 +53,13 @@ struct SweepArgs {
     const int *active;          // [S] samples still iterating
     long long cells;            // J * NXP
 };
+// The X-Y sweep adds the moments of the dense mode (mom = 0) to part[sample]
+// (vector atomics; the combine reads and clears them) and stores those of the
+// moment modes to part[item].
 
 struct CombineArgs {
     int S, MOM, chunks;
-    int zero_part;              // 1: one part array per sample, read and cleared (3D)
+    int zero_part;              // 1: one accumulated part array per sample, read and cleared
     long long cells4;           // J * NXP / 4
     long long cells;
     float g;                    // linear-kernel asymmetry (MOM = 3)

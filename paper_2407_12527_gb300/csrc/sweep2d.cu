@@ -87,6 +87,25 @@ __device__ __forceinline__ float2 shfl1(float2 v)
 
 __device__ __forceinline__ void ld8(const float *__restrict__ p, float (&v)[kCols]) { ldg8_early(p, v); }
 __device__ __forceinline__ void st8(float *__restrict__ p, const float (&v)[kCols]) { stg8(p, v); }
+// add 8 moments to the sample's accumulator: two 4-wide vector reductions
+__device__ __forceinline__ void red8(float *p, const float (&v)[kCols])
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+                 "f"(v[2]), "f"(v[3])
+                 : "memory");
+    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p + 4), "f"(v[4]), "f"(v[5]),
+                 "f"(v[6]), "f"(v[7])
+                 : "memory");
+}
+// the moments of a row: the dense mode (MOM = 0: many items per sample) adds them
+// to the sample's accumulator, the moment modes store them in the item's own
+// partial array (summed in item order by the combine)
+template <int MOM>
+__device__ __forceinline__ void put8(float *p, const float (&v)[kCols])
+{
+    if constexpr (MOM == 0) red8(p, v);
+    else stg8(p, v);
+}
 // psi of 8 cells as BF16 parts in one 32-byte sector, [8 hi | 8 lo] (the byte
 // layout of the FP32 array): hi = v rounded to the nearest BF16 on its bit
 // pattern (add half a BF16 unit, clear the low 16 bits; ties away from zero;
@@ -295,7 +314,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &A, int blk, bool yn
             float v[kCols];
 #pragma unroll
             for (int r = 0; r < kCols; ++r) v[r] = hsum(acc0[r]);
-            st8(part_i + ra.base + h * ra.rs, v);
+            put8<MOM>(part_i + ra.base + h * ra.rs, v);
             if constexpr (MOM == 0) {
 #pragma unroll
                 for (int k = 0; k < G; ++k) {
@@ -307,10 +326,10 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &A, int blk, bool yn
             if (MOM == 3) {
 #pragma unroll
                 for (int r = 0; r < kCols; ++r) v[r] = hsum(acc1[r]);
-                st8(part_i + A.cells + ra.base + h * ra.rs, v);
+                put8<MOM>(part_i + A.cells + ra.base + h * ra.rs, v);
 #pragma unroll
                 for (int r = 0; r < kCols; ++r) v[r] = hsum(acc2[r]);
-                st8(part_i + 2 * A.cells + ra.base + h * ra.rs, v);
+                put8<MOM>(part_i + 2 * A.cells + ra.base + h * ra.rs, v);
             }
         }
     }
@@ -360,7 +379,9 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
     for (int m = 0; m < NS; ++m)
         srcp[m] = MOM == 0 ? A.src + (long long)o.ord[m] * A.cells
                            : A.src + ((long long)it.sample * MOM + m) * A.cells;
-    float *part_i = A.part + (long long)blockIdx.x * n_out(MOM) * A.cells;
+    // moments: the sample's accumulator (dense mode) or the item's own partial array
+    float *part_i = A.part + (long long)(MOM == 0 ? it.sample : (int)blockIdx.x) *
+                                 n_out(MOM) * A.cells;
 
     // The rows of the lane's block for step t + PD are loaded at the start of
     // step t into a ring of PD + 1 register buffers indexed by t (the same index
@@ -424,7 +445,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
                 if (blk * kH + h < A.J)
 #pragma unroll
                     for (int m = 0; m < (STORE_LATE ? n_out(MOM) : 1); ++m)
-                        st8(part_i + m * A.cells + ra.base + h * ra.rs, out[m][h]);
+                        put8<MOM>(part_i + m * A.cells + ra.base + h * ra.rs, out[m][h]);
         }
         if (nwarps > 1) {
             const int lane = g & 31, w = g >> 5;
