@@ -143,6 +143,127 @@ __global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
     }
 }
 
+// 3D: phi of each sample from its two diagonal-storage accumulators (read and
+// cleared), the residual partials against the previous phi, and the next
+// source sigma_S phi + q in both diagonal families.  phi, sigma_S and q are kept
+// in family-0 storage too, and the threads walk that storage in order (one
+// 8-cell sector each, padding sectors skipped), so that only the family-1
+// accumulator and source are visited out of order.
+__global__ void __launch_bounds__(256) combine3_kernel(const Combine3Args A)
+{
+    const int s = blockIdx.y;
+    if (!A.active[s]) return;
+    const Skew3 g = A.sk;
+    const int n_sec = (int)(g.cells / 8);
+    float *acc0 = A.acc + (long long)s * g.cells;
+    float *acc1 = A.acc + ((long long)A.S + s) * g.cells;
+    float *src0 = A.src + (long long)s * g.cells;
+    float *src1 = A.src + ((long long)A.S + s) * g.cells;
+    float *phi = A.phi + (long long)s * g.cells;
+    float d2f = 0.f, n2f = 0.f;
+    for (int sec = blockIdx.x * blockDim.x + threadIdx.x; sec < n_sec;
+         sec += gridDim.x * blockDim.x) {
+        // sec = ((diag * L + strip) * 4 + hh) * NBg + jb
+        int t = sec / g.NBg;
+        const int jb = sec - t * g.NBg;
+        const int hh = t & 3;
+        t >>= 2;
+        const int diag = t / g.L, strip = t - diag * g.L;
+        const int k = diag - jb, j = 4 * jb + hh;
+        if (k < 0 || k >= g.K || j >= g.J) continue;
+        const long long i0 = (long long)sec * 8, i1 = skew3_index(g, 1, k, j, strip);
+        float a0[8], a1[8], old[8], ss[8], qq[8], now[8], out[8], zero[8];
+        ld8_volatile(acc0 + i0, a0);
+        ld8_volatile(acc1 + i1, a1);
+        ld8_volatile(phi + i0, old);
+        ldg8(A.sigma_s + i0, ss);
+        ldg8(A.q + i0, qq);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            zero[e] = 0.f;
+            now[e] = a0[e] + a1[e];
+            const float dd = now[e] - old[e];
+            d2f = fmaf(dd, dd, d2f);
+            n2f = fmaf(now[e], now[e], n2f);
+            out[e] = fmaf(ss[e], now[e], qq[e]);
+        }
+        stg8(acc0 + i0, zero);
+        stg8(acc1 + i1, zero);
+        stg8(phi + i0, now);
+        stg8(src0 + i0, out);
+        stg8(src1 + i1, out);
+    }
+    __shared__ double red[2][32];
+    double d2 = warp_sum((double)d2f);
+    double n2 = warp_sum((double)n2f);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][w] = d2;
+        red[1][w] = n2;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        d2 = lane < nw ? red[0][lane] : 0.0;
+        n2 = lane < nw ? red[1][lane] : 0.0;
+        d2 = warp_sum(d2);
+        n2 = warp_sum(n2);
+        if (lane == 0) {
+            A.partials[((long long)s * A.chunks + blockIdx.x) * 2 + 0] = d2;
+            A.partials[((long long)s * A.chunks + blockIdx.x) * 2 + 1] = n2;
+        }
+    }
+}
+
+// 3D average / extraction from family-0 diagonal storage [S][sk.cells] into [K][J][I]
+__global__ void average3_kernel(const float *phi, int S, Skew3 g, int I, double *avg, double *sum)
+{
+    const long long n = (long long)I * g.J * g.K;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const long long row = v / I;
+        const int i = (int)(v - row * I);
+        const int k = (int)(row / g.J), j = (int)(row - (long long)k * g.J);
+        const long long o = skew3_index(g, 0, k, j, i >> 3) + (i & 7);
+        double acc = 0.0;
+        for (int s = 0; s < S; ++s) acc += (double)phi[(long long)s * g.cells + o];
+        if (sum) sum[v] = acc;
+        if (avg) avg[v] = S > 0 ? acc / S : 0.0;
+    }
+}
+__global__ void extract3_kernel(const float *phi, int sample, Skew3 g, int I, double *out)
+{
+    const long long n = (long long)I * g.J * g.K;
+    const float *p = phi + (long long)sample * g.cells;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const long long row = v / I;
+        const int i = (int)(v - row * I);
+        const int k = (int)(row / g.J), j = (int)(row - (long long)k * g.J);
+        out[v] = (double)p[skew3_index(g, 0, k, j, i >> 3) + (i & 7)];
+    }
+}
+
+// dst[f][copy][sk.cells] = in[K][J][NXP] in diagonal family f < n_fam, for every copy
+__global__ void skew3_scatter_kernel(const float *in, Skew3 g, int NXP, int n_fam, int n_copies,
+                                     float *dst)
+{
+    const long long n_sec = (long long)g.K * g.J * g.L;
+    for (long long sec = (long long)blockIdx.x * blockDim.x + threadIdx.x; sec < n_sec;
+         sec += (long long)gridDim.x * blockDim.x) {
+        const long long row = sec / g.L;
+        const int strip = (int)(sec - row * g.L);
+        const int k = (int)(row / g.J), j = (int)(row - (long long)k * g.J);
+        float v[8];
+        ldg8(in + row * NXP + strip * 8, v);
+        for (int f = 0; f < n_fam; ++f) {
+            const long long i = skew3_index(g, f, k, j, strip);
+            for (int c = 0; c < n_copies; ++c)
+                stg8(dst + ((long long)f * n_copies + c) * g.cells + i, v);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) finalize_kernel(const FinalizeArgs A)
 {
     int cnt = 0;
@@ -187,7 +308,7 @@ __global__ void init_state_kernel(int S, int MOM, long long cells, const float *
         const long long cell = v % cells;
         const int m = (int)((v / cells) % MOM);
         phi[v] = 0.f;
-        src[v] = m == 0 ? q[cell] : 0.f;  // psi^0 = 0: the first source is q
+        if (src) src[v] = m == 0 ? q[cell] : 0.f;  // psi^0 = 0: the first source is q
     }
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < S) {
@@ -272,6 +393,40 @@ cudaError_t launch_combine(const CombineArgs &a, cudaStream_t st)
     if (a.MOM == 1) combine_kernel<1><<<grid, block, 0, st>>>(a);
     else if (a.MOM == 3) combine_kernel<3><<<grid, block, 0, st>>>(a);
     else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine3(const Combine3Args &a, cudaStream_t st)
+{
+    const dim3 grid(a.chunks, a.S), block(256);
+    combine3_kernel<<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_average3(const float *phi, int S, const Skew3 &sk, int I, double *avg,
+                            double *sum, cudaStream_t st)
+{
+    average3_kernel<<<blocks_for((long long)I * sk.J * sk.K, 256), 256, 0, st>>>(phi, S, sk, I,
+                                                                                 avg, sum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract3(const float *phi, int sample, const Skew3 &sk, int I, double *out,
+                            cudaStream_t st)
+{
+    extract3_kernel<<<blocks_for((long long)I * sk.J * sk.K, 256), 256, 0, st>>>(phi, sample, sk,
+                                                                                 I, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_skew3_scatter(const float *in, const Skew3 &sk, int NXP, int n_fam,
+                                 int n_copies, float *dst, cudaStream_t st)
+{
+    const long long n_sec = (long long)sk.K * sk.J * sk.L;
+    long long b = (n_sec + 255) / 256;
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    skew3_scatter_kernel<<<(unsigned)b, 256, 0, st>>>(in, sk, NXP, n_fam, n_copies, dst);
     return cudaGetLastError();
 }
 

@@ -94,6 +94,9 @@ struct rom_ctx {
     // 3D: CTA item lists (one octant each) and the tile hand-off buffers
     std::vector<int> cta_begin, cta_list;
     DevBuf cta_begin_dev, cta_list_dev, xface, yface, err3;
+    // 3D diagonal storage: sigma_T [2], source and flux [2][S], sigma_S and q (family 0);
+    // phi is kept in family 0 as well ([S][sk.cells])
+    DevBuf sig3, src3, acc3, ss3, q3;
     int n_ctas3 = 0, nwarps3 = 1, n_tx = 1, n_ty = 1;
 
     // dense scattering operator (mode 0); tensor-core variant: split BF16 psi and A
@@ -263,6 +266,8 @@ int set_grid_common(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3
 // GB size).  The moment modes in X-Y keep the per-item partials: few items per
 // sample, bitwise reproducible sums, and faster there.
 bool accumulates(const rom_ctx *ctx) { return ctx->dim == 3 || ctx->MOM == 0; }
+// 3D keeps its accumulators (and source, sigma_T) in diagonal storage, not in part
+bool uses_part(const rom_ctx *ctx) { return ctx->dim == 2; }
 
 int source_mode(const rom_ctx *ctx)
 {
@@ -511,9 +516,11 @@ romk::Sweep3Args sweep3_args(const rom_ctx *ctx)
     a.inv_dx = (float)(ctx->I / (ctx->hi[0] - ctx->lo[0]));
     a.inv_dy = (float)(ctx->J / (ctx->hi[1] - ctx->lo[1]));
     a.inv_dz = (float)(ctx->K / (ctx->hi[2] - ctx->lo[2]));
-    a.sigma_t = (const float *)ctx->sigt.p;
-    a.src = (const float *)ctx->src.p;
-    a.phi = (float *)ctx->part.p;
+    a.sk = romk::make_skew3(ctx->J, ctx->K, ctx->NXP);
+    a.sigma_t = (const float *)ctx->sig3.p;
+    a.src = (const float *)ctx->src3.p;
+    a.phi = (float *)ctx->acc3.p;
+    a.S = ctx->S;
     a.items = (const SweepItem *)ctx->items_dev.p;
     a.cta_begin = (const int *)ctx->cta_begin_dev.p;
     a.cta_list = (const int *)ctx->cta_list_dev.p;
@@ -697,7 +704,22 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     ca.q = (const float *)ctx->q.p;
     ca.active = (const int *)ctx->active.p;
     ca.partials = (double *)ctx->partials.p;
-    CK(romk::launch_combine(ca, st));
+    if (ctx->dim == 3) {
+        romk::Combine3Args c3{};
+        c3.S = ctx->S;
+        c3.chunks = ctx->chunks;
+        c3.sk = romk::make_skew3(ctx->J, ctx->K, ctx->NXP);
+        c3.acc = (float *)ctx->acc3.p;
+        c3.src = (float *)ctx->src3.p;
+        c3.phi = (float *)ctx->phi.p;
+        c3.sigma_s = (const float *)ctx->ss3.p;
+        c3.q = (const float *)ctx->q3.p;
+        c3.active = (const int *)ctx->active.p;
+        c3.partials = (double *)ctx->partials.p;
+        CK(romk::launch_combine3(c3, st));
+    } else {
+        CK(romk::launch_combine(ca, st));
+    }
     if (ctx->MOM == 0) {
         if (k2) CK(cudaEventRecord(k2, st));
         if (ctx->opt.dense_precision == 1) {
@@ -879,7 +901,8 @@ void rom_destroy(rom_ctx *ctx)
                       &ctx->active, &ctx->iters, &ctx->flags, &ctx->resid, &ctx->n_active,
                       &ctx->avg, &ctx->sum, &ctx->tmp, &ctx->psi, &ctx->src_ord, &ctx->Amat,
                       &ctx->dtab, &ctx->z32, &ctx->cta_begin_dev, &ctx->cta_list_dev,
-                      &ctx->xface, &ctx->yface, &ctx->err3, &ctx->psi_split,
+                      &ctx->xface, &ctx->yface, &ctx->err3, &ctx->sig3, &ctx->src3,
+                      &ctx->acc3, &ctx->ss3, &ctx->q3, &ctx->psi_split,
                       &ctx->a_hi, &ctx->a_lo, &ctx->tc_err};
     for (DevBuf *b : bufs) release(*b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -1347,12 +1370,30 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     if (chunks != ctx->chunks) invalidate_graph(ctx);
     ctx->chunks = chunks;
     const int MOM = ctx->MOM == 0 ? 1 : ctx->MOM;  // moments kept per sample
-    const size_t state = (size_t)ctx->S * MOM * cells * sizeof(float);
+    // 3D keeps phi in family-0 diagonal storage and its source in src3 only
+    const size_t state = ctx->dim == 3 ? (size_t)ctx->S * romk::make_skew3(ctx->J, ctx->K,
+                                                                            ctx->NXP).cells *
+                                             sizeof(float)
+                                       : (size_t)ctx->S * MOM * cells * sizeof(float);
+    const size_t src_bytes = ctx->dim == 3 ? 0 : state;
     const size_t nI = (size_t)n_cells(ctx);
     // part: the moments of each sample accumulated by the sweep, or of each work item
-    const size_t part_units = accumulates(ctx) ? (size_t)ctx->S : ctx->items.size();
-    void *before[] = {ctx->phi.p, ctx->src.p, ctx->part.p, ctx->partials.p, ctx->active.p};
-    if ((rc = ensure(ctx, ctx->phi, state)) || (rc = ensure(ctx, ctx->src, state)) ||
+    const size_t part_units = !uses_part(ctx)   ? 0
+                              : accumulates(ctx) ? (size_t)ctx->S
+                                                 : ctx->items.size();
+    if (ctx->dim == 3) {
+        const romk::Skew3 sk = romk::make_skew3(ctx->J, ctx->K, ctx->NXP);
+        if (sk.cells >= (1LL << 31))
+            return fail(ctx, ROM_ERR_UNSUPPORTED, "3D grid too large for one sample's arrays");
+        const size_t b = (size_t)sk.cells * sizeof(float);
+        if ((rc = ensure(ctx, ctx->sig3, 2 * b)) || (rc = ensure(ctx, ctx->src3, 2 * ctx->S * b)) ||
+            (rc = ensure(ctx, ctx->acc3, 2 * ctx->S * b)) || (rc = ensure(ctx, ctx->ss3, b)) ||
+            (rc = ensure(ctx, ctx->q3, b)))
+            return rc;
+    }
+    void *before[] = {ctx->phi.p,    ctx->src.p,  ctx->part.p, ctx->partials.p, ctx->active.p,
+                      ctx->sig3.p,   ctx->src3.p, ctx->acc3.p, ctx->ss3.p,      ctx->q3.p};
+    if ((rc = ensure(ctx, ctx->phi, state)) || (rc = ensure(ctx, ctx->src, src_bytes)) ||
         (rc = ensure(ctx, ctx->part, part_units * MOM * cells * sizeof(float))) ||
         (rc = ensure(ctx, ctx->partials, (size_t)ctx->S * chunks * 2 * sizeof(double))) ||
         (rc = ensure(ctx, ctx->active, ctx->S * sizeof(int))) ||
@@ -1376,19 +1417,41 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
             return rc;
         invalidate_graph(ctx);
     }
-    void *after[] = {ctx->phi.p, ctx->src.p, ctx->part.p, ctx->partials.p, ctx->active.p};
+    void *after[] = {ctx->phi.p,  ctx->src.p,  ctx->part.p, ctx->partials.p, ctx->active.p,
+                     ctx->sig3.p, ctx->src3.p, ctx->acc3.p, ctx->ss3.p,      ctx->q3.p};
     if (memcmp(before, after, sizeof before) != 0) invalidate_graph(ctx);
 
     const long long launches0 = ctx->launches;
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     if (ctx->MOM == 0 && ctx->opt.dense_precision == 1)
         CK(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), ctx->stream));
-    if (accumulates(ctx))  // the sweep accumulates into part; the combine clears it
+    if (uses_part(ctx) && accumulates(ctx))  // the sweep accumulates; the combine clears it
         CK(cudaMemsetAsync(ctx->part.p, 0, part_units * MOM * cells * sizeof(float), ctx->stream));
-    if (ctx->dim == 3) CK(cudaMemsetAsync(ctx->err3.p, 0, sizeof(int), ctx->stream));
-    CK(romk::launch_init_state(ctx->S, MOM, cells, (const float *)ctx->q.p, (float *)ctx->phi.p,
-                               (float *)ctx->src.p, (int *)ctx->active.p, (int *)ctx->iters.p,
-                               (int *)ctx->flags.p, (double *)ctx->resid.p, ctx->stream));
+    if (ctx->dim == 3) {
+        // diagonal storage: sigma_T (both families), the first source q of every
+        // sample, sigma_S and q for the combine (family 0), cleared accumulators, phi = 0
+        const romk::Skew3 sk = romk::make_skew3(ctx->J, ctx->K, ctx->NXP);
+        CK(cudaMemsetAsync(ctx->err3.p, 0, sizeof(int), ctx->stream));
+        CK(cudaMemsetAsync(ctx->acc3.p, 0, 2 * (size_t)ctx->S * sk.cells * sizeof(float),
+                           ctx->stream));
+        CK(romk::launch_skew3_scatter((const float *)ctx->sigt.p, sk, ctx->NXP, 2, 1,
+                                      (float *)ctx->sig3.p, ctx->stream));
+        CK(romk::launch_skew3_scatter((const float *)ctx->q.p, sk, ctx->NXP, 2, ctx->S,
+                                      (float *)ctx->src3.p, ctx->stream));
+        CK(romk::launch_skew3_scatter((const float *)ctx->sigs.p, sk, ctx->NXP, 1, 1,
+                                      (float *)ctx->ss3.p, ctx->stream));
+        CK(romk::launch_skew3_scatter((const float *)ctx->q.p, sk, ctx->NXP, 1, 1,
+                                      (float *)ctx->q3.p, ctx->stream));
+        ctx->launches += 4;
+        CK(romk::launch_init_state(ctx->S, 1, sk.cells, nullptr, (float *)ctx->phi.p, nullptr,
+                                   (int *)ctx->active.p, (int *)ctx->iters.p, (int *)ctx->flags.p,
+                                   (double *)ctx->resid.p, ctx->stream));
+    } else {
+        CK(romk::launch_init_state(ctx->S, MOM, cells, (const float *)ctx->q.p,
+                                   (float *)ctx->phi.p, (float *)ctx->src.p, (int *)ctx->active.p,
+                                   (int *)ctx->iters.p, (int *)ctx->flags.p,
+                                   (double *)ctx->resid.p, ctx->stream));
+    }
     ++ctx->launches;
     if (ctx->MOM == 0) {  // psi^0 = 0: every ordinate's first source is q
         CK(romk::launch_dense_init((const float *)ctx->q.p, cells, ctx->Mtot,
@@ -1443,8 +1506,14 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
             if (n_active == 0) break;
         }
     }
-    CK(romk::launch_average((const float *)ctx->phi.p, ctx->S, MOM, ctx->I, (int)ctx->rows,
-                            ctx->NXP, (double *)ctx->avg.p, (double *)ctx->sum.p, ctx->stream));
+    if (ctx->dim == 3)
+        CK(romk::launch_average3((const float *)ctx->phi.p, ctx->S,
+                                 romk::make_skew3(ctx->J, ctx->K, ctx->NXP), ctx->I,
+                                 (double *)ctx->avg.p, (double *)ctx->sum.p, ctx->stream));
+    else
+        CK(romk::launch_average((const float *)ctx->phi.p, ctx->S, MOM, ctx->I, (int)ctx->rows,
+                                ctx->NXP, (double *)ctx->avg.p, (double *)ctx->sum.p,
+                                ctx->stream));
     ++ctx->launches;
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     ctx->h_iters.assign(ctx->S, 0);
@@ -1503,6 +1572,17 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     return ROM_OK;
 }
 
+// phi of one sample -> out[n_cells] (device), from the layout its dimension keeps
+cudaError_t extract_phi(rom_ctx *ctx, int sample, double *out)
+{
+    if (ctx->dim == 3)
+        return romk::launch_extract3((const float *)ctx->phi.p, sample,
+                                     romk::make_skew3(ctx->J, ctx->K, ctx->NXP), ctx->I, out,
+                                     ctx->stream);
+    return romk::launch_extract((const float *)ctx->phi.p, sample, ctx->MOM == 0 ? 1 : ctx->MOM,
+                                ctx->I, (int)ctx->rows, ctx->NXP, out, ctx->stream);
+}
+
 int rom_get_scalar_flux(rom_ctx *ctx, int sample, double *out)
 {
     if (!ctx || !out) return fail(ctx, ROM_ERR_INVALID_ARG, "NULL argument");
@@ -1513,9 +1593,7 @@ int rom_get_scalar_flux(rom_ctx *ctx, int sample, double *out)
     if (sample >= 0) {
         int rc = ensure(ctx, ctx->tmp, nI * sizeof(double));
         if (rc) return rc;
-        CK(romk::launch_extract((const float *)ctx->phi.p, sample, ctx->MOM == 0 ? 1 : ctx->MOM,
-                                ctx->I, (int)ctx->rows, ctx->NXP, (double *)ctx->tmp.p,
-                                ctx->stream));
+        CK(extract_phi(ctx, sample, (double *)ctx->tmp.p));
         ++ctx->launches;
         CK(cudaMemcpyAsync(out, ctx->tmp.p, nI * sizeof(double), cudaMemcpyDeviceToHost,
                            ctx->stream));
@@ -1535,8 +1613,7 @@ int rom_get_scalar_flux_device(rom_ctx *ctx, int sample, double *out)
     CK(cudaSetDevice(ctx->device));
     const size_t nI = (size_t)n_cells(ctx);
     if (sample >= 0) {
-        CK(romk::launch_extract((const float *)ctx->phi.p, sample, ctx->MOM == 0 ? 1 : ctx->MOM,
-                                ctx->I, (int)ctx->rows, ctx->NXP, out, ctx->stream));
+        CK(extract_phi(ctx, sample, out));
         ++ctx->launches;
     } else {
         CK(cudaMemcpyAsync(out, ctx->avg.p, nI * sizeof(double), cudaMemcpyDeviceToDevice,

@@ -72,14 +72,49 @@ struct CombineArgs {
     double *partials;           // [S][chunks][2]
 };
 
+// Diagonal storage of 3D cell arrays read or written by the sweep (source, sigma_T,
+// flux accumulators).  Cell (i, j, k) with row block jb = j / 4, row hh = j % 4,
+// strip = i / 8, c = i % 8 sits at
+//   ((((diag * L + strip) * 4 + hh) * NBg + jb) * 8 + c,
+//   family 0 ("plus", octants whose y and z directions agree): diag = k + jb,
+//   family 1 ("minus"):                                        diag = k - jb + NBg - 1,
+// with L = NXP / 8 strips, NBg = ceil(J / 4) blocks and K + NBg - 1 diagonals.  The
+// lanes of a sweep warp sit on one diagonal at consecutive blocks, so each of
+// their row accesses is one contiguous kilobyte.
+struct Skew3 {
+    int J, K, L, NBg;
+    long long DS;     // floats per diagonal: L * 4 * NBg * 8
+    long long cells;  // floats per array: (K + NBg - 1) * DS
+};
+__host__ __device__ inline Skew3 make_skew3(int J, int K, int NXP)
+{
+    Skew3 g;
+    g.J = J;
+    g.K = K;
+    g.L = NXP / 8;
+    g.NBg = (J + 3) / 4;
+    g.DS = (long long)g.L * 4 * g.NBg * 8;
+    g.cells = (long long)(K + g.NBg - 1) * g.DS;
+    return g;
+}
+// offset of the 8-cell sector (k, j, strip) in family f
+__host__ __device__ inline long long skew3_index(const Skew3 &g, int f, int k, int j, int strip)
+{
+    const int jb = j >> 2, hh = j & 3;
+    const long long diag = f == 0 ? (long long)k + jb : (long long)k - jb + g.NBg - 1;
+    return diag * g.DS + (((long long)strip * 4 + hh) * g.NBg + jb) * 8;
+}
+
 // 3D sweep (K9): G = 1 or 2 ordinates of one sample and octant per work item,
 // CTAs over lists of items of one octant, x-y tiles swept by successive launches.
 struct Sweep3Args {
     int I, J, K, NXP;
     float inv_dx, inv_dy, inv_dz;
-    const float *sigma_t;       // [K][J][NXP]
-    const float *src;           // [S][K][J][NXP] isotropic source sigma_S phi + q
-    float *phi;                 // [S][K][J][NXP] flux accumulated by the sweep
+    Skew3 sk;                   // diagonal storage of the three arrays below
+    const float *sigma_t;       // [family][sk.cells]
+    const float *src;           // [family][S][sk.cells] isotropic source sigma_S phi + q
+    float *phi;                 // [family][S][sk.cells] flux accumulated by the sweep
+    int S;
     const SweepItem *items;     // quad = octant bits, ord[0] the ordinate
     const int *cta_begin;       // [n_ctas + 1] ranges of cta_list
     const int *cta_list;        // item indices, one octant per CTA
@@ -217,6 +252,27 @@ cudaError_t launch_sweep3d(const Sweep3Args &a, int n_ctas, int nwarps, int G, i
 int sweep3d_ctas_per_sm(int nwarps, int G);
 int sweep3d_tile_cols();  // x extent of a 3D tile (8-column strips x warps per CTA)
 cudaError_t launch_combine(const CombineArgs &a, cudaStream_t st);
+// 3D: phi = the sum of the two accumulators, residual partials, and the next
+// source sigma_S phi + q in both diagonal families; phi, sigma_S, q in family 0.
+struct Combine3Args {
+    int S, chunks;
+    Skew3 sk;
+    float *acc;                 // [2][S][sk.cells], cleared after reading
+    float *src;                 // [2][S][sk.cells]
+    float *phi;                 // [S][sk.cells] (family 0)
+    const float *sigma_s, *q;   // [sk.cells] (family 0)
+    const int *active;
+    double *partials;           // [S][chunks][2]
+};
+cudaError_t launch_combine3(const Combine3Args &a, cudaStream_t st);
+cudaError_t launch_average3(const float *phi, int S, const Skew3 &sk, int I, double *avg,
+                            double *sum, cudaStream_t st);
+cudaError_t launch_extract3(const float *phi, int sample, const Skew3 &sk, int I, double *out,
+                            cudaStream_t st);
+// copies of a [K][J][NXP] array into diagonal families 0 .. n_fam-1, n_copies
+// times per family (dst[f][copy][sk.cells]); padding entries are left as they are
+cudaError_t launch_skew3_scatter(const float *in, const Skew3 &sk, int NXP, int n_fam,
+                                 int n_copies, float *dst, cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t st);
 cudaError_t launch_init_state(int S, int MOM, long long cells, const float *q, float *phi,
                               float *src, int *active, int *iters, int *flags, double *resid,

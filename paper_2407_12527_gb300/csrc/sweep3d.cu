@@ -30,7 +30,10 @@
 // latency overlaps a whole step), and the flux accumulation, one vector
 // reduction (red.global.add.v4.f32) per 4 cells and item into the sample's
 // phi: no per-item partial arrays, whose size (cells x ordinates) would
-// exceed the flux itself by the ordinate count.  Two ordinates share each
+// exceed the flux itself by the ordinate count.  Those three arrays are kept
+// in diagonal storage (Skew3): the 32 lanes of a warp sit on one diagonal of
+// the (plane, row block) wavefront at consecutive blocks, so every row access
+// of a warp instruction is one contiguous kilobyte instead of 32 lines.  Two ordinates share each
 // source load and flux reduction and run as FP32x2 pairs (__ffma2_rn ...).
 // With 255 registers per thread a CTA is 8 warps, one per SM.  Wider x-y
 // extents are cut into tiles swept by successive launches in upwind order; a
@@ -159,7 +162,7 @@ __device__ __forceinline__ void block_diag(
     const typename V3<G>::T abe, const typename V3<G>::T wg, const typename V3<G>::T (&xin)[kH3],
     typename V3<G>::T (&y)[kCols], typename V3<G>::T (&z)[kH3][kCols], float (&pS)[kH3][kCols],
     float (&pT)[kH3][kCols], const bool (&rok)[kH3], const bool (&cok)[kCols], float *phi_k,
-    const float *sp2, const float *tp2, const int (&jrow)[kH3], int NXP, bool act2,
+    const float *sp2, const float *tp2, const int (&rowpart)[kH3], bool act2,
     typename V3<G>::T (&xo)[kH3])
 {
     using T = typename V3<G>::T;
@@ -196,10 +199,10 @@ __device__ __forceinline__ void block_diag(
         if (hf >= 0 && hf < kH3) {
             xo[hf] = x[hf];
             if (!CHECK || rok[hf]) {
-                red8(phi_k + (long long)jrow[hf] * NXP, out[hf]);
+                red8(phi_k + rowpart[hf], out[hf]);
                 if (act2) {
-                    ldg8_early(sp2 + (long long)jrow[hf] * NXP, pS[hf]);
-                    ldg8_early(tp2 + (long long)jrow[hf] * NXP, pT[hf]);
+                    ldg8_early(sp2 + rowpart[hf], pS[hf]);
+                    ldg8_early(tp2 + rowpart[hf], pT[hf]);
                 }
             }
         }
@@ -215,16 +218,23 @@ __device__ __forceinline__ void sweep3_body(const Sweep3Args &A, Smem3 &sm, int 
     const int ls0 = A.tile_x * kStrips;       // first strip of the tile (upwind order)
     const int nw = min(kStrips, L - ls0);
     if (w >= nw) return;
+    // rows counted from the inflow side over Jp = 4 ceil(J / 4) rows: with s < 0 the
+    // count starts at row Jp - 1, so the 4-row blocks of every lane are aligned
+    const int Jp = 4 * A.sk.NBg;
     const int jt0 = A.tile_y * kTileRows;     // first row of the tile (upwind order)
-    const int nrows = min(kTileRows, A.J - jt0);
-    const int NB = (nrows + kH3 - 1) / kH3;   // lanes with rows
+    const int nrows = min(kTileRows, Jp - jt0);
+    const int NB = nrows / kH3;               // lanes with rows
     const bool yneg = (oct >> 1) & 1, zneg = (oct >> 2) & 1;
     const int col0 = (XNEG ? (L - 1 - (ls0 + w)) : (ls0 + w)) * kCols;
     const bool first_x = w == 0, last_x = w == nw - 1;
     const bool up_x = A.tile_x > 0, down_x = A.tile_x + 1 < A.n_tx;
     const bool up_y = A.tile_y > 0, down_y = A.tile_y + 1 < A.n_ty;
     const int I = A.I, J = A.J, K = A.K, NXP = A.NXP;
-    const long long plane = (long long)J * NXP;
+    const long long plane = A.sk.DS;  // one z-plane further: one diagonal further
+    const int fam = yneg == zneg ? 0 : 1;
+    const float *const sig_f = A.sigma_t + (long long)fam * A.sk.cells;
+    const float *const src_f = A.src + (long long)fam * A.S * A.sk.cells;
+    float *const phi_f = A.phi + (long long)fam * A.S * A.sk.cells;
     const long long fx = (long long)K * J, fy = (long long)K * I, fz = (long long)J * I;
     const float f = SCHEME == 0 ? 2.f : 1.f;
     const int n_items = sm.n_list;
@@ -232,21 +242,23 @@ __device__ __forceinline__ void sweep3_body(const Sweep3Args &A, Smem3 &sm, int 
 
     int jrow[kH3];
     bool rok[kH3];
+    int rowpart[kH3];  // diagonal-storage offset of the row at plane 0 (sk.cells < 2^31)
 #pragma unroll
     for (int h = 0; h < kH3; ++h) {
         const int r = lane * kH3 + h;  // row within the tile, upwind order
-        rok[h] = r < nrows;
         const int jl = jt0 + r;
-        jrow[h] = yneg ? J - 1 - jl : jl;
+        jrow[h] = yneg ? Jp - 1 - jl : jl;
+        rok[h] = r < nrows && jrow[h] >= 0 && jrow[h] < J;
+        rowpart[h] = rok[h] ? (int)skew3_index(A.sk, fam, 0, jrow[h], col0 / kCols) : 0;
     }
     bool cok[kCols];
 #pragma unroll
     for (int r = 0; r < kCols; ++r) cok[r] = col0 + r < I;
     // warp-uniform: every lane's block is 4 full rows of 8 valid cells
-    const bool full = col0 + kCols <= I && nrows % kH3 == 0;
+    const bool full = col0 + kCols <= I && J == Jp;
 
     T a = vsplat<T>(0.f), b = a, e = a, abe = vsplat<T>(1.f), wg = a;
-    float *phip = A.phi;
+    float *phip = phi_f;
     int item = 0;
     T z[kH3][kCols], y[kCols], xin[kH3];
     float pS[kH3][kCols], pT[kH3][kCols];  // the lane's rows for the current step
@@ -262,13 +274,13 @@ __device__ __forceinline__ void sweep3_body(const Sweep3Args &A, Smem3 &sm, int 
     // stream position of the lane at step t: p = t - lane, item n = p / K, plane kl = p % K
     int kl = -lane, n = 0;
     if (lane == 0 && n_items > 0 && 0 < NB) {  // rows of the first step
-        const long long off = (long long)(zneg ? K - 1 : 0) * plane + col0;
-        const float *sp = A.src + (long long)sm.sample[0] * A.cells + off;
+        const long long off = (long long)(zneg ? K - 1 : 0) * plane;
+        const float *sp = src_f + (long long)sm.sample[0] * A.sk.cells + off;
 #pragma unroll
         for (int h = 0; h < kH3; ++h)
             if (rok[h]) {
-                ldg8_early(sp + (long long)jrow[h] * NXP, pS[h]);
-                ldg8_early(A.sigma_t + off + (long long)jrow[h] * NXP, pT[h]);
+                ldg8_early(sp + rowpart[h], pS[h]);
+                ldg8_early(sig_f + off + rowpart[h], pT[h]);
             }
     }
 
@@ -296,7 +308,7 @@ __device__ __forceinline__ void sweep3_body(const Sweep3Args &A, Smem3 &sm, int 
                 vset(abe, g, ag + bg + eg);
                 vset(wg, g, g < A.items[item].n ? A.ow[o] : 0.f);
             }
-            phip = A.phi + (long long)sm.sample[n] * A.cells;
+            phip = phi_f + (long long)sm.sample[n] * A.sk.cells;
             const long long zf = 2 * fx + 2 * fy + (zneg ? fz : 0);
 #pragma unroll
             for (int h = 0; h < kH3; ++h)
@@ -370,25 +382,25 @@ __device__ __forceinline__ void sweep3_body(const Sweep3Args &A, Smem3 &sm, int 
         }
         // the rows of the next step are loaded as soon as this step has used them
         const int k2 = zneg ? K - 1 - kl2 : kl2;
-        const long long off2 = (long long)k2 * plane + col0;
-        const float *sp2 = A.src + (long long)sm.sample[act2 ? n2 : 0] * A.cells + off2;
-        const float *tp2 = A.sigma_t + off2;
+        const long long off2 = (long long)k2 * plane;
+        const float *sp2 = src_f + (long long)sm.sample[act2 ? n2 : 0] * A.sk.cells + off2;
+        const float *tp2 = sig_f + off2;
         T xo[kH3];
-        const long long pk = (long long)k * plane + col0;
+        const long long pk = (long long)k * plane;
         if (act) {
             if (full)
                 block_diag<G, SCHEME, XNEG, false>(a, b, e, abe, wg, xin, y, z, pS, pT, rok, cok,
-                                                    phip + pk, sp2, tp2, jrow, NXP, act2, xo);
+                                                    phip + pk, sp2, tp2, rowpart, act2, xo);
             else
                 block_diag<G, SCHEME, XNEG, true>(a, b, e, abe, wg, xin, y, z, pS, pT, rok, cok,
-                                                   phip + pk, sp2, tp2, jrow, NXP, act2, xo);
+                                                   phip + pk, sp2, tp2, rowpart, act2, xo);
         } else {
 #pragma unroll
             for (int h = 0; h < kH3; ++h) {
                 xo[h] = vsplat<T>(0.f);
                 if (act2 && rok[h]) {
-                    ldg8_early(sp2 + (long long)jrow[h] * NXP, pS[h]);
-                    ldg8_early(tp2 + (long long)jrow[h] * NXP, pT[h]);
+                    ldg8_early(sp2 + rowpart[h], pS[h]);
+                    ldg8_early(tp2 + rowpart[h], pT[h]);
                 }
             }
         }
