@@ -613,3 +613,64 @@ def test_example21_ray_effect_measure_dom():
         assert o.M == int(M)
         got = O.e_inf(_solve(p, o, tol=1e-10), ref)
         assert abs(got - float(want)) <= 0.5e-4, (N, got, want)
+
+
+# ---------------------------------------------------- ROM statistics (P11)
+
+def _slope(x, y):
+    return float(np.polyfit(np.log(x), np.log(y), 1)[0])
+
+
+def test_randomized_quadrature_error_order_one_dimension():
+    """Sec. 3.2: one uniform point per subinterval of a uniform mesh of n cells
+    gives an integration error of order n^(-3/2) (independent cells, variance per
+    cell ~ h^2).  With one zeta cell (n_zeta = 1) the ROM set is stratified in
+    theta alone, so for f depending on the azimuth only the RMS error over draws
+    must fall as n_theta^(-3/2); unstratified draws would give n^(-1/2)."""
+    from scipy.integrate import quad
+
+    def f(t):
+        return np.exp(np.sin(t) + 0.5 * np.cos(t))
+
+    exact = quad(f, -np.pi, np.pi)[0] / (2 * np.pi)
+    ns = [4, 8, 16, 32, 64]
+    rms = []
+    for n in ns:
+        err = [np.sum(o.w * f(np.arctan2(o.s, o.c))) - exact
+               for o in (O.rom_ordinates_xy(777, k, 1, n) for k in range(400))]
+        rms.append(np.sqrt(np.mean(np.square(err))))
+    assert -1.7 < _slope(ns, rms) < -1.3
+
+
+def test_randomized_quadrature_error_order_two_dimensions():
+    """The same argument on the (zeta, theta) partition of Sec. 3.1 with
+    n x n cells per quadrant (m = n^2 points): variance per cell ~ h^2 / m^2 with
+    h ~ m^(-1/2), m cells, so the RMS error falls as m^(-1) for a smooth f."""
+    z, wz = np.polynomial.legendre.leggauss(200)
+    z, wz = 0.5 * (z + 1), wz / 2
+    th = np.linspace(0, 2 * np.pi, 2000, endpoint=False)
+    Z, T = np.meshgrid(z, th, indexing="ij")
+    c, s = np.sqrt(1 - Z ** 2) * np.cos(T), np.sqrt(1 - Z ** 2) * np.sin(T)
+    exact = np.sum(wz[:, None] * (np.exp(c + 0.5 * s) + Z ** 2 * c ** 2)) / th.size
+    ns = [2, 4, 8, 16]
+    rms = []
+    for n in ns:
+        err = [np.sum(o.w * (np.exp(o.c + 0.5 * o.s) + o.zeta ** 2 * o.c ** 2)) - exact
+               for o in (O.rom_ordinates_xy(778, k, n, n) for k in range(400))]
+        rms.append(np.sqrt(np.mean(np.square(err))))
+    assert -1.2 < _slope(np.square(ns), rms) < -0.8
+
+
+def test_mc_error_order_in_number_of_samples():
+    """Sec. 4.1-4.2 (eq. 1dMCerror): the distance of the average of t ROM samples
+    from E[phi] falls as t^(-1/2).  E[phi] is the mean of 2048 samples (M = 4,
+    Example 2.1 on 20 x 20); e_MC(t) is the RMS over disjoint groups of t.  A
+    generator whose samples shared draws would flatten the slope."""
+    p = W.example_2_1(I=20, J=20)
+    N = 2048
+    sets = [O.rom_ordinates_xy(779, k, 1, 1) for k in range(N)]
+    phi = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, sets, tol=1e-12)["phi"]
+    E = phi.mean(0)
+    ts = [4, 8, 16, 32, 64]
+    em = [np.sqrt(np.mean((phi.reshape(N // t, t, p.J, p.I).mean(1) - E) ** 2)) for t in ts]
+    assert -0.65 < _slope(ts, em) < -0.4
