@@ -129,3 +129,19 @@ def test_tc_rejects_more_than_128_ordinates(rom):
         ctx.solve()
     assert e.value.code == -7
     ctx.close()
+
+
+def test_tc_hg_disc_full_size_sampled(rom):
+    """The 512 x 512 Henyey-Greenstein workload in the benchmark's launch
+    configuration (32 samples x 128 ordinates, tensor-core contraction, device-side
+    loop) at 3 sweeps; samples 0 and 31 against the oracle."""
+    p = W.hg_disc()
+    seed = W.ordinate_seed(3)
+    S = 32
+    gpu = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, seed, [4] * S, [8] * S,
+                    fixed_iters=3, dense_precision=1)
+    for k in (0, 31):
+        ref = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q,
+                         [O.rom_ordinates_xy(seed, k, 4, 8)], kernel="hg", g=0.8,
+                         fixed_iters=3)
+        assert rel(gpu["phi"][k], ref["phi"][0]) < TOL, k

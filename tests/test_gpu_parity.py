@@ -357,3 +357,24 @@ def test_dense_operator_equals_moment_path(rom, kernel, g):
                   kernel=kernel, g=g, fixed_iters=6, dense_source=1)
     for k in range(2):
         assert rel(b["phi"][k], a["phi"][k]) < TOL
+
+
+def test_checkerboard_full_size_sampled(rom):
+    """The 448 x 448 checkerboard workload (256 samples, M uniform in {8, 16, 32, 64},
+    partitions as in the benchmark, autotuned work-item size, device-side loop) at
+    4 sweeps; the first sample of each M is solved by the oracle."""
+    p = W.checkerboard()
+    parts = [W.partition(m) for m in p.ordinates["m_quadrant"]]
+    nz, nt = [a for a, _ in parts], [b for _, b in parts]
+    seed = W.ordinate_seed(2)
+    gpu = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, seed=seed, nz=nz,
+                    nt=nt, fixed_iters=4, tile_g=-1)
+    firsts = {}
+    for k, m in enumerate(p.ordinates["m_quadrant"]):
+        firsts.setdefault(m, k)
+    assert len(firsts) == 4
+    for m, k in sorted(firsts.items()):
+        ref = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q,
+                         [O.rom_ordinates_xy(seed, k, nz[k], nt[k])], fixed_iters=4)
+        assert rel(gpu["phi"][k], ref["phi"][0]) < TOL, (m, k)
+    assert list(gpu["iters"]) == [4] * len(nz)
