@@ -215,7 +215,10 @@ long long face_offset(const rom_ctx *ctx, int face)
 long long n_cells(const rom_ctx *ctx) { return (long long)ctx->I * ctx->J * ctx->K; }
 long long padded_cells(const rom_ctx *ctx) { return ctx->rows * ctx->NXP; }
 
-int set_grid_common(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3],
+// prev: the context held a valid grid before this call.  A grid of the same shape
+// and extent keeps the work items, the tuned work-item size, the buffers and the
+// captured graph (only the coefficient arrays change); any inflow is dropped.
+int set_grid_common(rom_ctx *ctx, bool prev, int dim, const int64_t n[3], const double lo[3],
                     const double hi[3])
 {
     if (dim != 2 && dim != 3) return fail(ctx, ROM_ERR_INVALID_ARG, "dim must be 2 or 3 (got %d)", dim);
@@ -231,6 +234,10 @@ int set_grid_common(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3
     for (int d = 0; d < dim; ++d)
         if (!(hi[d] > lo[d]) || !isfinite(lo[d]) || !isfinite(hi[d]))
             return fail(ctx, ROM_ERR_INVALID_ARG, "need hi > lo (finite)");
+    bool same = prev && ctx->dim == dim && ctx->I == (int)n[0] && ctx->J == (int)n[1] &&
+                ctx->K == (dim == 3 ? (int)n[2] : 1);
+    for (int d = 0; d < 3 && same; ++d)
+        same = ctx->lo[d] == (d < dim ? lo[d] : 0.0) && ctx->hi[d] == (d < dim ? hi[d] : 1.0);
     ctx->dim = dim;
     ctx->I = (int)n[0];
     ctx->J = (int)n[1];
@@ -241,21 +248,40 @@ int set_grid_common(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3
         ctx->lo[d] = d < dim ? lo[d] : 0.0;
         ctx->hi[d] = d < dim ? hi[d] : 1.0;
     }
+    bool had_inflow = false;
     for (int f = 0; f < 6; ++f) {
+        had_inflow |= !ctx->inflow_iso[f].empty() || !ctx->inflow_ord[f].empty();
         ctx->inflow_iso[f].clear();
         ctx->inflow_ord[f].clear();
     }
-    ctx->inflow_dirty = true;
-    ctx->items_dirty = true;
-    ctx->tuned_g = 0;
     ctx->solved = false;
-    invalidate_graph(ctx);
+    if (!same) {
+        ctx->inflow_dirty = true;
+        ctx->items_dirty = true;
+        ctx->tuned_g = 0;
+        invalidate_graph(ctx);
+    } else if (had_inflow) {
+        ctx->inflow_dirty = true;  // re-uploaded (as vacuum) by the next solve
+    }
     const size_t bytes = (size_t)padded_cells(ctx) * sizeof(float);
     int rc;
     if ((rc = ensure(ctx, ctx->sigt, bytes)) || (rc = ensure(ctx, ctx->sigs, bytes)) ||
         (rc = ensure(ctx, ctx->q, bytes)))
         return rc;
     return ROM_OK;
+}
+
+// Uniform sigma_T selects the sweep variant and enters its arguments: a change
+// re-tunes the work-item size and rebuilds the graph.
+void set_homog(rom_ctx *ctx, bool homog, float sigma_t)
+{
+    if (homog != ctx->homog || sigma_t != ctx->sigma_t_homog) {
+        ctx->tuned_g = 0;
+        ctx->items_dirty = true;
+        invalidate_graph(ctx);
+    }
+    ctx->homog = homog;
+    ctx->sigma_t_homog = sigma_t;
 }
 
 // 1: isotropic moment, 3: linear-kernel moments, 0: dense operator
@@ -957,6 +983,7 @@ int rom_set_grid(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3], 
     if (!ctx) return ROM_ERR_INVALID_ARG;
     if (!sigma_t || !sigma_s || !q) return fail(ctx, ROM_ERR_INVALID_ARG, "NULL coefficient array");
     CK(cudaSetDevice(ctx->device));
+    const bool prev = ctx->grid_set;
     ctx->grid_set = false;
     if ((dim == 2 || dim == 3) && n && n[0] >= 1 && n[1] >= 1 && (dim == 2 || n[2] >= 1) &&
         n[0] <= 4096 && n[1] <= 4096 && (dim == 2 || n[2] <= 4096)) {
@@ -969,7 +996,7 @@ int rom_set_grid(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3], 
                             a, b, c);
         }
     }
-    int rc = set_grid_common(ctx, dim, n, lo, hi);
+    int rc = set_grid_common(ctx, prev, dim, n, lo, hi);
     if (rc) return rc;
     const int I = ctx->I, NXP = ctx->NXP;
     const long long J = ctx->rows;  // 3D: the K * J rows of [K][J][I]
@@ -991,8 +1018,7 @@ int rom_set_grid(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3], 
                 hq[d] = 0.f;
             }
         }
-    ctx->homog = ((float)mn == (float)mx);
-    ctx->sigma_t_homog = (float)mn;
+    set_homog(ctx, (float)mn == (float)mx, (float)mn);
     const size_t bytes = hs.size() * sizeof(float);
     CK(cudaMemcpyAsync(ctx->sigt.p, hs.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->sigs.p, hss.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
@@ -1009,8 +1035,9 @@ int rom_set_grid_device(rom_ctx *ctx, int dim, const int64_t n[3], const double 
     if (!ctx) return ROM_ERR_INVALID_ARG;
     if (!sigma_t || !sigma_s || !q) return fail(ctx, ROM_ERR_INVALID_ARG, "NULL coefficient array");
     CK(cudaSetDevice(ctx->device));
+    const bool prev = ctx->grid_set;
     ctx->grid_set = false;
-    int rc = set_grid_common(ctx, dim, n, lo, hi);
+    int rc = set_grid_common(ctx, prev, dim, n, lo, hi);
     if (rc) return rc;
     if ((rc = ensure(ctx, ctx->tmp, 4 * sizeof(unsigned int)))) return rc;
     unsigned int init[3] = {0x7f800000u, 0u, 0u};  // +inf bits, 0, 0
@@ -1028,8 +1055,7 @@ int rom_set_grid_device(rom_ctx *ctx, int dim, const int64_t n[3], const double 
     float mn, mx;
     memcpy(&mn, &st[0], sizeof mn);
     memcpy(&mx, &st[1], sizeof mx);
-    ctx->homog = (mn == mx);
-    ctx->sigma_t_homog = mn;
+    set_homog(ctx, mn == mx, mn);
     ctx->grid_set = true;
     return ROM_OK;
 }
@@ -1230,8 +1256,15 @@ int set_ordinates_seeded(rom_ctx *ctx, uint64_t seed, int first_sample, int n_sa
     ctx->ord_source = ORD_SEED;
     ctx->seed_octants = octants;
     if (layout_same) {
-        // same sample layout: work items, buffers and the captured graph stay valid
-        for (int f = 0; f < 6; ++f) ctx->inflow_ord[f].clear();
+        // same sample layout: work items, buffers and the captured graph stay valid;
+        // the dense operator belongs to the old ordinates, and so does per-ordinate inflow
+        bool had_ord_inflow = false;
+        for (int f = 0; f < 6; ++f) {
+            had_ord_inflow |= !ctx->inflow_ord[f].empty();
+            ctx->inflow_ord[f].clear();
+        }
+        if (had_ord_inflow) ctx->inflow_dirty = true;
+        ctx->pmat_dirty = true;
         ctx->solved = false;
     } else {
         reset_ordinate_dependents(ctx);

@@ -378,3 +378,82 @@ def test_checkerboard_full_size_sampled(rom):
                          [O.rom_ordinates_xy(seed, k, nz[k], nt[k])], fixed_iters=4)
         assert rel(gpu["phi"][k], ref["phi"][0]) < TOL, (m, k)
     assert list(gpu["iters"]) == [4] * len(nz)
+
+
+# -------------------------------------------- context reuse between solves
+
+def _phis(ctx):
+    return np.stack([ctx.scalar_flux(k) for k in range(ctx.n_samples)])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_reseed_same_layout_rebuilds_dense_operator(rom, precision):
+    """A second seeded set with the same sample layout keeps the work items and the
+    graph, but the dense operator A = w_l' P(u_l', u_l) must follow the new ordinates."""
+    I, J = 40, 36
+    st, ss, q = W.random_medium(I, J, seed=81, ratio_max=0.8)
+    ctx = rom.RomContext(0)
+    ctx.set_grid(I, J, (0, 1, 0, 1), st, ss, q)
+    ctx.set_kernel("hg", 0.7)
+    ctx.set_options(fixed_iters=4, dense_precision=precision)
+    ctx.set_ordinates_seed(91, [2, 2], [3, 3])
+    ctx.solve()
+    ctx.set_ordinates_seed(91, [2, 2], [3, 3], first_sample=5)
+    ctx.solve()
+    gpu = _phis(ctx)
+    ctx.close()
+    for k in range(2):
+        ref = O.solve_xy(I, J, (0, 1, 0, 1), st, ss, q, [O.rom_ordinates_xy(91, 5 + k, 2, 3)],
+                         kernel="hg", g=0.7, fixed_iters=4)
+        assert rel(gpu[k], ref["phi"][0]) < TOL, k
+
+
+def test_reseed_same_layout_drops_per_ordinate_inflow(rom):
+    I, J = 30, 26
+    st, ss, q = W.random_medium(I, J, seed=83)
+    per = W.random_inflow(I, J, seed=84, per_ordinate_M=16)
+    off = [0, J, 2 * J, 2 * J + I, 2 * J + 2 * I]
+    ctx = rom.RomContext(0)
+    ctx.set_grid(I, J, (0, 1, 0, 1), st, ss, q)
+    ctx.set_options(fixed_iters=4)
+    ctx.set_ordinates_seed(93, [2], [2])
+    for f in range(4):
+        ctx.set_inflow_ordinates(f, np.ascontiguousarray(per[:, off[f]:off[f + 1]]))
+    ctx.solve()
+    ctx.set_ordinates_seed(93, [2], [2], first_sample=1)
+    ctx.solve()
+    gpu = _phis(ctx)
+    ctx.close()
+    ref = O.solve_xy(I, J, (0, 1, 0, 1), st, ss, q, [O.rom_ordinates_xy(93, 1, 2, 2)],
+                     fixed_iters=4)
+    assert rel(gpu[0], ref["phi"][0]) < TOL
+
+
+def test_set_grid_same_shape_new_coefficients(rom):
+    """A new grid of the same shape and extent keeps the captured graph; the solve
+    must see the new coefficients (uniform -> varying sigma_T switches the sweep
+    variant), and inflow set for the old grid is dropped."""
+    I, J = 48, 40
+    bounds = (0, 1, 0, 1)
+    ctx = rom.RomContext(0)
+    ctx.set_options(fixed_iters=5)
+    ctx.set_grid(I, J, bounds, 1.0, 0.6, 1.0)
+    ctx.set_ordinates_seed(95, [2, 1], [2, 3])
+    ctx.set_inflow_isotropic(0, np.full(J, 0.5))
+    ctx.solve()
+    sets = [O.rom_ordinates_xy(95, k, nz, nt) for k, (nz, nt) in enumerate([(2, 2), (1, 3)])]
+    for seed in (86, 87):
+        st, ss, q = W.random_medium(I, J, seed=seed)
+        ctx.set_grid(I, J, bounds, st, ss, q)
+        ctx.solve()
+        gpu = _phis(ctx)
+        ref = O.solve_xy(I, J, bounds, st, ss, q, sets, fixed_iters=5)["phi"]
+        for k in range(2):
+            assert rel(gpu[k], ref[k]) < TOL, (seed, k)
+    ctx.set_grid(I, J, bounds, 1.3, 0.9, 0.5)  # back to uniform sigma_T
+    ctx.solve()
+    gpu = _phis(ctx)
+    ctx.close()
+    ref = O.solve_xy(I, J, bounds, 1.3, 0.9, 0.5, sets, fixed_iters=5)["phi"]
+    for k in range(2):
+        assert rel(gpu[k], ref[k]) < TOL, k
