@@ -57,8 +57,15 @@ __device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float2 add_(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float neg_(float a) { return -a; }
 __device__ __forceinline__ float2 neg_(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
-__device__ __forceinline__ float2 rcp_(float2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+// 1 / (sigma_T + a + b) of a cell with varying sigma_T: the hardware reciprocal
+// (rcp.approx, within 1 ulp; the argument is >= sigma_T > 0, never subnormal)
+__device__ __forceinline__ float rcp_(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float2 rcp_(float2 a) { return make_float2(rcp_(a.x), rcp_(a.y)); }
 __device__ __forceinline__ float hsum(float a) { return a; }
 __device__ __forceinline__ float hsum(float2 a) { return a.x + a.y; }
 __device__ __forceinline__ void setc(float &a, int, float v) { a = v; }
