@@ -103,6 +103,10 @@ typedef struct rom_options {
                      /* bf16(v - v_hi); psi kept as BF16 hi/lo, the bytes of FP32; at most */
                      /* 128 ordinates per sample and 2048 samples per context, else        */
                      /* ROM_ERR_UNSUPPORTED)                                               */
+    int rows_per_step; /* X-Y sweep: grid rows a lane advances per wavefront step; 0 = 4,  */
+                     /* or the measured choice with tile_g = -1 (2 or 4); 2 or 4 forces it  */
+                     /* (2 only in the isotropic and linear-kernel moment modes, the dense */
+                     /* operator mode runs 4); other values are ROM_ERR_INVALID_ARG        */
 } rom_options;
 
 /* Statistics of the last rom_solve. */
@@ -120,6 +124,9 @@ typedef struct rom_stats {
     double source_ms;        /* summed duration of the dense-operator contractions        */
     int64_t source_launches; /* contractions timed (dense operator only)                  */
     int tile_g;              /* ordinates per sweep work item used by this solve          */
+    int rows_per_step;       /* X-Y sweep: grid rows a lane advances per wavefront step    */
+                             /* (4, or 2 when the tile_g = -1 autotuner finds it faster    */
+                             /* in the moment modes); 0 for 3D grids                       */
 } rom_stats;
 
 /* ------------------------------------------------------------- lifetime */

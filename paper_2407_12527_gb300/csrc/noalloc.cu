@@ -256,7 +256,7 @@ extern "C" int rom_sweep_xy_noalloc(void *cuda_stream, int I, int J, double dx, 
     a.active = (const int *)(base + o_active);
     a.cells = (long long)cells;
     const int L = (I + romk::kCols - 1) / romk::kCols;
-    NA_CK(romk::launch_sweep2d(a, n_items, (L + 31) / 32, kG, scheme, false, 1, st));
+    NA_CK(romk::launch_sweep2d(a, n_items, (L + 31) / 32, kG, scheme, false, 1, 4, st));
     noalloc_sum_kernel<<<blocks((long long)n_samples * J * I), 256, 0, st>>>(
         part, (const int *)(base + o_begin), n_samples, I, J, NXP, phi);
     NA_CK(cudaGetLastError());

@@ -87,7 +87,9 @@ struct rom_ctx {
     // work items
     bool items_dirty = true;
     int G_used = 0;
+    int H_used = 4;   // X-Y sweep: rows a lane advances per wavefront step
     int tuned_g = 0;  // measured choice (tile_g = -1), valid while the layout is unchanged
+    int tuned_h = 0;  // rows per step of that choice
     std::vector<SweepItem> items;
     std::vector<int> item_begin;
     DevBuf items_dev, item_begin_dev;
@@ -187,6 +189,7 @@ void reset_ordinate_dependents(rom_ctx *ctx)
 {
     ctx->pmat_dirty = true;
     ctx->tuned_g = 0;
+    ctx->tuned_h = 0;
     for (int f = 0; f < 6; ++f) ctx->inflow_ord[f].clear();
     ctx->inflow_dirty = true;
     ctx->items_dirty = true;
@@ -259,6 +262,7 @@ int set_grid_common(rom_ctx *ctx, bool prev, int dim, const int64_t n[3], const 
         ctx->inflow_dirty = true;
         ctx->items_dirty = true;
         ctx->tuned_g = 0;
+        ctx->tuned_h = 0;
         invalidate_graph(ctx);
     } else if (had_inflow) {
         ctx->inflow_dirty = true;  // re-uploaded (as vacuum) by the next solve
@@ -277,6 +281,7 @@ void set_homog(rom_ctx *ctx, bool homog, float sigma_t)
 {
     if (homog != ctx->homog || sigma_t != ctx->sigma_t_homog) {
         ctx->tuned_g = 0;
+        ctx->tuned_h = 0;
         ctx->items_dirty = true;
         invalidate_graph(ctx);
     }
@@ -301,6 +306,16 @@ int source_mode(const rom_ctx *ctx)
     if (ctx->kernel_kind == ROM_KERNEL_ISO) return 1;
     if (ctx->kernel_kind == ROM_KERNEL_LINEAR && ctx->kernel_flags == 0) return 3;
     return 0;
+}
+
+// rows per wavefront step of the X-Y sweep: forced by the option, else the autotuned
+// value (moment modes), else 4
+int choose_rows(const rom_ctx *ctx)
+{
+    if (ctx->dim != 2 || source_mode(ctx) == 0) return 4;
+    if (ctx->opt.rows_per_step == 2 || ctx->opt.rows_per_step == 4) return ctx->opt.rows_per_step;
+    if (ctx->opt.tile_g == -1 && ctx->tuned_h > 0) return ctx->tuned_h;
+    return 4;
 }
 
 int choose_g(const rom_ctx *ctx)
@@ -415,6 +430,7 @@ int build_items(rom_ctx *ctx)
     if (ctx->dim == 3) return build_items3(ctx);
     const int G = choose_g(ctx);
     ctx->G_used = G;
+    ctx->H_used = choose_rows(ctx);
     ctx->items.clear();
     ctx->item_begin.assign(ctx->S + 1, 0);
     std::vector<int> byq[4];
@@ -711,7 +727,7 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
         const int L = (ctx->I + romk::kCols - 1) / romk::kCols;
         const int nwarps = (L + 31) / 32;
         CK(romk::launch_sweep2d(sa, (int)ctx->items.size(), nwarps, ctx->G_used, ctx->opt.scheme,
-                                ctx->homog, ctx->MOM, st));
+                                ctx->homog, ctx->MOM, ctx->H_used, st));
     }
     if (k1) CK(cudaEventRecord(k1, st));
     romk::CombineArgs ca{};
@@ -784,18 +800,20 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     return ROM_OK;
 }
 
-// tile_g = -1: time the sweep kernel of every candidate work-item size on the
-// current problem (three sweeps after one warm-up, from the initial source) and
-// keep the fastest.
+// tile_g = -1: time the sweep kernel of every candidate work-item size G and
+// rows per wavefront step H (2 only in the moment modes) on the current problem
+// (three sweeps after one warm-up, from the initial source) and keep the fastest.
 int autotune_g(rom_ctx *ctx)
 {
     const int cap = source_mode(ctx) == 0 ? 2 : 4;
     const long long cells = (long long)ctx->J * ctx->NXP;
     const int MOMk = ctx->MOM == 0 ? 1 : ctx->MOM;
     float best_ms = 0.f;
-    int best = 0, rc;
-    for (int G : {1, 2, 4}) {
-        if (G > cap) continue;
+    int best = 0, best_h = 4, rc;
+    const int want_h = source_mode(ctx) == 0 ? 4 : ctx->opt.rows_per_step;  // 0: both
+    for (int cand = 0; cand < 6; ++cand) {
+        const int G = (1 << (cand >> 1)), H = (cand & 1) ? 2 : 4;
+        if (G > cap || (want_h != 0 && H != want_h)) continue;
         ctx->opt.tile_g = G;
         if ((rc = build_items(ctx))) return rc;
         const size_t units = accumulates(ctx) ? (size_t)ctx->S : ctx->items.size();
@@ -813,7 +831,7 @@ int autotune_g(rom_ctx *ctx)
         for (int rep = 0; rep < 4; ++rep) {
             if (rep == 1) CK(cudaEventRecord(ctx->ev0, ctx->stream));
             CK(romk::launch_sweep2d(sa, (int)ctx->items.size(), (L + 31) / 32, G, ctx->opt.scheme,
-                                    ctx->homog, ctx->MOM, ctx->stream));
+                                    ctx->homog, ctx->MOM, H, ctx->stream));
             ++ctx->launches;
         }
         CK(cudaEventRecord(ctx->ev1, ctx->stream));
@@ -822,11 +840,13 @@ int autotune_g(rom_ctx *ctx)
         CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
         if (best == 0 || ms < best_ms) {
             best = G;
+            best_h = H;
             best_ms = ms;
         }
     }
     ctx->opt.tile_g = -1;
     ctx->tuned_g = best;
+    ctx->tuned_h = best_h;
     ctx->items_dirty = true;
     return ROM_OK;
 }
@@ -884,6 +904,7 @@ void rom_default_options(rom_options *opt)
     opt->time_kernels = 0;
     opt->dense_source = 0;
     opt->dense_precision = 0;
+    opt->rows_per_step = 0;
 }
 
 int rom_create(rom_ctx **out, int cuda_device)
@@ -967,8 +988,11 @@ int rom_set_options(rom_ctx *ctx, const rom_options *opt)
         return fail(ctx, ROM_ERR_INVALID_ARG, "dense_source must be 0 or 1");
     if (opt->dense_precision != 0 && opt->dense_precision != 1)
         return fail(ctx, ROM_ERR_INVALID_ARG, "dense_precision must be 0 or 1");
+    if (opt->rows_per_step != 0 && opt->rows_per_step != 2 && opt->rows_per_step != 4)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "rows_per_step must be 0, 2 or 4");
     if (opt->tile_g != ctx->opt.tile_g || opt->dense_source != ctx->opt.dense_source ||
-        opt->dense_precision != ctx->opt.dense_precision) {
+        opt->dense_precision != ctx->opt.dense_precision ||
+        opt->rows_per_step != ctx->opt.rows_per_step) {
         ctx->items_dirty = true;
         ctx->pmat_dirty = true;
     }
@@ -1362,6 +1386,7 @@ int rom_set_kernel(rom_ctx *ctx, int kind, double g, int flags)
     ctx->kernel_flags = flags;
     ctx->pmat_dirty = true;
     ctx->tuned_g = 0;
+    ctx->tuned_h = 0;
     ctx->items_dirty = true;
     ctx->solved = false;
     invalidate_graph(ctx);
@@ -1595,6 +1620,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     st.source_ms = source_ms;
     st.source_launches = source_launches;
     st.tile_g = ctx->G_used;
+    st.rows_per_step = ctx->dim == 2 ? ctx->H_used : 0;
     if (device_loop) ctx->launches += (long long)launches_per_iteration(ctx) * st.iterations_max;
     st.kernel_launches = ctx->launches - launches0;
     if (stats_out) *stats_out = st;

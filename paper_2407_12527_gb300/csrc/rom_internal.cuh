@@ -245,8 +245,11 @@ __device__ __forceinline__ void stg8(float *p, const float (&v)[8])
 
 // mom: 1 isotropic, 3 linear-kernel moments, 0 dense kernel (per-ordinate
 // source in, psi out).
+// rows: rows a lane advances per wavefront step, 4 (every mode) or 2 (mom 1, 3).
 cudaError_t launch_sweep2d(const SweepArgs &a, int n_items, int nwarps, int G, int scheme,
-                           bool homog, int mom, cudaStream_t st);
+                           bool homog, int mom, int rows, cudaStream_t st);
+cudaError_t launch_sweep2d_rows2(const SweepArgs &a, int n_items, int nwarps, int G, int scheme,
+                                 bool homog, int mom, cudaStream_t st);
 cudaError_t launch_sweep3d(const Sweep3Args &a, int n_ctas, int nwarps, int G, int scheme,
                            cudaStream_t st);
 int sweep3d_ctas_per_sm(int nwarps, int G);

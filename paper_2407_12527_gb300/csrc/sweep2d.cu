@@ -27,553 +27,22 @@
 // block are loaded one step ahead into registers.  No ordinate or cell values
 // are stored: only the moments of each item, which a later kernel sums per
 // sample.
-#include <cuda_bf16.h>
-
-#include "rom_internal.cuh"
+//
+// The kernels live in sweep2d_impl.cuh; this unit compiles them for H = 4 rows
+// per step (every source mode) and sweep2d_h2.cu for H = 2 (moment modes), the
+// better shape for large batches, picked by the work-item autotuner.
+#define SWEEP2D_ROWS 4
+#define SWEEP2D_WITH_DENSE 1
+#include "sweep2d_impl.cuh"
 
 namespace romk {
-namespace {
-
-constexpr int kH = 4;        // rows per lane per wavefront step
-constexpr int kPrefetch = 1;  // steps between the load of a block's rows and their use
-
-// ---- packs: one ordinate (float), or two ordinates (float2, FP32x2 ops)
-template <int G>
-struct Pack {
-    using T = float2;
-    static constexpr int N = G / 2;
-};
-template <>
-struct Pack<1> {
-    using T = float;
-    static constexpr int N = 1;
-};
-
-__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ float2 fma_(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float2 mul_(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float2 add_(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float neg_(float a) { return -a; }
-__device__ __forceinline__ float2 neg_(float2 a) { return make_float2(-a.x, -a.y); }
-// 1 / (sigma_T + a + b) of a cell with varying sigma_T: the hardware reciprocal
-// (rcp.approx, within 1 ulp; the argument is >= sigma_T > 0, never subnormal)
-__device__ __forceinline__ float rcp_(float a)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
-    return r;
-}
-__device__ __forceinline__ float2 rcp_(float2 a) { return make_float2(rcp_(a.x), rcp_(a.y)); }
-__device__ __forceinline__ float hsum(float a) { return a; }
-__device__ __forceinline__ float hsum(float2 a) { return a.x + a.y; }
-__device__ __forceinline__ void setc(float &a, int, float v) { a = v; }
-__device__ __forceinline__ void setc(float2 &a, int i, float v)
-{
-    if (i) a.y = v;
-    else a.x = v;
-}
-template <class T>
-__device__ __forceinline__ T splat(float s);
-template <>
-__device__ __forceinline__ float splat<float>(float s) { return s; }
-template <>
-__device__ __forceinline__ float2 splat<float2>(float s) { return make_float2(s, s); }
-
-template <bool DOWN>
-__device__ __forceinline__ float shfl1(float v)
-{
-    return DOWN ? __shfl_down_sync(0xffffffffu, v, 1) : __shfl_up_sync(0xffffffffu, v, 1);
-}
-template <bool DOWN>
-__device__ __forceinline__ float2 shfl1(float2 v)
-{
-    return make_float2(shfl1<DOWN>(v.x), shfl1<DOWN>(v.y));
-}
-
-__device__ __forceinline__ void ld8(const float *__restrict__ p, float (&v)[kCols]) { ldg8_early(p, v); }
-__device__ __forceinline__ void st8(float *__restrict__ p, const float (&v)[kCols]) { stg8(p, v); }
-// add 8 moments to the sample's accumulator: two 4-wide vector reductions
-__device__ __forceinline__ void red8(float *p, const float (&v)[kCols])
-{
-    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(v[0]), "f"(v[1]),
-                 "f"(v[2]), "f"(v[3])
-                 : "memory");
-    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p + 4), "f"(v[4]), "f"(v[5]),
-                 "f"(v[6]), "f"(v[7])
-                 : "memory");
-}
-// the moments of a row: the dense mode (MOM = 0: many items per sample) adds them
-// to the sample's accumulator, the moment modes store them in the item's own
-// partial array (summed in item order by the combine)
-template <int MOM>
-__device__ __forceinline__ void put8(float *p, const float (&v)[kCols])
-{
-    if constexpr (MOM == 0) red8(p, v);
-    else stg8(p, v);
-}
-// psi of 8 cells as BF16 parts in one 32-byte sector, [8 hi | 8 lo] (the byte
-// layout of the FP32 array): hi = v rounded to the nearest BF16 on its bit
-// pattern (add half a BF16 unit, clear the low 16 bits; ties away from zero;
-// two packed by one byte permute), lo = bf16_rn(v - hi) (the difference is exact
-// in FP32; two converted by one packed conversion).  hi + lo carries 16
-// significant bits of v, and lo has either sign, so the lo * lo term the
-// product drops has no bias.
-__device__ __forceinline__ void st8_split(uint32_t *psi2, long long off, const float (&v)[kCols])
-{
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const uint32_t b0 = (__float_as_uint(v[2 * e]) + 0x8000u) & 0xFFFF0000u;
-        const uint32_t b1 = (__float_as_uint(v[2 * e + 1]) + 0x8000u) & 0xFFFF0000u;
-        h[e] = __byte_perm(b0, b1, 0x7632);
-        const float r0 = v[2 * e] - __uint_as_float(b0);
-        const float r1 = v[2 * e + 1] - __uint_as_float(b1);
-        const __nv_bfloat162 lo2 = __floats2bfloat162_rn(r0, r1);
-        l[e] = *reinterpret_cast<const uint32_t *>(&lo2);
-    }
-    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(psi2 + off), "r"(h[0]),
-                 "r"(h[1]), "r"(h[2]), "r"(h[3]), "r"(l[0]), "r"(l[1]), "r"(l[2]), "r"(l[3])
-                 : "memory");
-}
-
-// Per-ordinate constants of a work item, grouped in packs.
-template <int G>
-struct OrdPacks {
-    using T = typename Pack<G>::T;
-    static constexpr int N = Pack<G>::N;
-    T a[N], b[N], ab[N], w[N], rd[N], c[N], s[N], wc[N], ws[N];
-    // uniform sigma_T: the cell update folded into one FMA per upwind chain
-    //   DD:   x_out  = al x + 2rd (S + b py),   al = 2a rd - 1
-    //         py_out = a2 x + 2rd S + be py,    a2 = 2a rd, be = 2b rd - 1
-    //         psi_c  = (x + x_out) / 2
-    //   step: psi_c  = ar x + rd (S + b py) = x_out = py_out,  ar = a rd, br = b rd
-    T al[N], a2[N], b2[N], be[N], r2[N], wh[N], ar[N], br[N];
-    int ord[G];
-};
-
-// Source modes (template parameter MOM): 1 isotropic (one source moment in,
-// phi out), 3 linear kernel (three source moments in, phi, Jx, Jy out), 0 dense
-// kernel (one source per ordinate in, psi of every ordinate and phi out).
-__host__ __device__ constexpr int n_src(int mom, int g) { return mom == 0 ? g : mom; }
-__host__ __device__ constexpr int n_out(int mom) { return mom == 0 ? 1 : mom; }
-
-// Arrays read per cell: NS sources, plus sigma_T when it varies.
-template <int NS, bool HOMOG>
-struct RowBuf {
-    static constexpr int NA = NS + (HOMOG ? 0 : 1);
-    float v[NA][kH][kCols];
-};
-
-// Offset of row h of block blk for the lane's columns: base + h * rs.
-struct RowAddr {
-    long long base, rs;
-    __device__ __forceinline__ RowAddr(const SweepArgs &A, int blk, bool yneg, int col0)
-    {
-        const int jl0 = blk * kH;
-        base = (long long)(yneg ? (A.J - 1 - jl0) : jl0) * A.NXP + col0;
-        rs = yneg ? -(long long)A.NXP : (long long)A.NXP;
-    }
-};
-
-// Issue the loads of the rows of block `blk` (rows past J are skipped).
-template <int NS, bool HOMOG>
-__device__ __forceinline__ void load_block(const SweepArgs &A, int blk, bool yneg, int col0,
-                                           const float *const (&srcp)[NS], RowBuf<NS, HOMOG> &b)
-{
-    const RowAddr ra(A, blk, yneg, col0);
-#pragma unroll
-    for (int h = 0; h < kH; ++h) {
-        if (blk * kH + h < A.J) {
-            const long long row = ra.base + h * ra.rs;
-#pragma unroll
-            for (int m = 0; m < NS; ++m) ld8(srcp[m] + row, b.v[m][h]);
-            if (!HOMOG) ld8(A.sigma_t + row, b.v[NS][h]);
-        }
-    }
-}
-
-// One H x 8 block of cells for all G ordinates of the item, from the rows in b.
-// Cell value psi_c of the ordinates of pack p at column r, kept for the row store.
-__device__ __forceinline__ void psi_put(float (&row)[1][kCols], int, int r, float v) { row[0][r] = v; }
-template <int R>
-__device__ __forceinline__ void psi_put(float (&row)[R][kCols], int p, int r, float2 v)
-{
-    if constexpr (R >= 2) {
-        row[(2 * p) % R][r] = v.x;
-        row[(2 * p + 1) % R][r] = v.y;
-    }
-}
-
-// The block's moments are left in out[][][] (LATE: the caller stores them
-// after the shuffle), or stored row by row at part_i (three moments: the
-// registers for holding them are not there).
-template <int G, int MOM, int SCHEME, bool HOMOG, bool XNEG, bool CHECK, bool LATE>
-__device__ __forceinline__ void sweep_block(const SweepArgs &A, int blk, bool yneg, int col0,
-                                            const OrdPacks<G> &o,
-                                            typename Pack<G>::T (&py)[kCols][Pack<G>::N],
-                                            const typename Pack<G>::T (&xin)[kH][Pack<G>::N],
-                                            typename Pack<G>::T (&xo)[kH][Pack<G>::N],
-                                            const RowBuf<n_src(MOM, G), HOMOG> &b,
-                                            float (&out)[LATE ? n_out(MOM) : 1][kH][kCols],
-                                            float *__restrict__ part_i)
-{
-    constexpr int NS = n_src(MOM, G);
-    using T = typename Pack<G>::T;
-    constexpr int N = Pack<G>::N;
-    const T two = splat<T>(2.f);
-#pragma unroll
-    for (int h = 0; h < kH; ++h) {
-        if (CHECK && blk * kH + h >= A.J) {
-#pragma unroll
-            for (int p = 0; p < N; ++p) xo[h][p] = splat<T>(0.f);
-            continue;
-        }
-        T x[N];
-#pragma unroll
-        for (int p = 0; p < N; ++p) x[p] = xin[h][p];
-        T acc0[kCols], acc1[kCols], acc2[kCols];
-#pragma unroll
-        for (int r = 0; r < kCols; ++r) acc0[r] = acc1[r] = acc2[r] = splat<T>(0.f);
-        float psi_row[MOM == 0 ? G : 1][kCols];  // dense mode: psi of the row, per ordinate
-#pragma unroll
-        for (int rr = 0; rr < kCols; ++rr) {
-            const int r = XNEG ? (kCols - 1 - rr) : rr;
-            const bool ok = !CHECK || (col0 + r < A.I);
-            const T s0 = splat<T>(b.v[0][h][r]);
-#pragma unroll
-            for (int p = 0; p < N; ++p) {
-                T S = s0;
-                if (MOM == 3)
-                    S = fma_(o.c[p], splat<T>(b.v[1][h][r]), fma_(o.s[p], splat<T>(b.v[2][h][r]), S));
-                if (MOM == 0) {  // per-ordinate sources of the pack
-                    if constexpr (G == 1) setc(S, 0, b.v[0][h][r]);
-                    else {
-                        setc(S, 0, b.v[(2 * p) % NS][h][r]);
-                        setc(S, 1, b.v[(2 * p + 1) % NS][h][r]);
-                    }
-                }
-                if (HOMOG && SCHEME == 0) {
-                    const T s2 = mul_(S, o.r2[p]);                 // 2 rd S
-                    const T xn = fma_(o.al[p], x[p], fma_(o.b2[p], py[r][p], s2));
-                    const T pyn = fma_(o.a2[p], x[p], fma_(o.be[p], py[r][p], s2));
-                    if (MOM == 0) psi_put(psi_row, p, r, mul_(add_(x[p], xn), splat<T>(0.5f)));
-                    if (ok) {
-                        acc0[r] = fma_(o.wh[p], add_(x[p], xn), acc0[r]);
-                        if (MOM == 3) {
-                            const T sm = add_(x[p], xn);
-                            acc1[r] = fma_(mul_(o.wc[p], splat<T>(0.5f)), sm, acc1[r]);
-                            acc2[r] = fma_(mul_(o.ws[p], splat<T>(0.5f)), sm, acc2[r]);
-                        }
-                        x[p] = xn;
-                        py[r][p] = pyn;
-                    }
-                } else if (HOMOG) {
-                    const T pc = fma_(o.ar[p], x[p], fma_(o.br[p], py[r][p], mul_(S, o.rd[p])));
-                    if (MOM == 0) psi_put(psi_row, p, r, pc);
-                    if (ok) {
-                        x[p] = pc;
-                        py[r][p] = pc;
-                        acc0[r] = fma_(o.w[p], pc, acc0[r]);
-                        if (MOM == 3) {
-                            acc1[r] = fma_(o.wc[p], pc, acc1[r]);
-                            acc2[r] = fma_(o.ws[p], pc, acc2[r]);
-                        }
-                    }
-                } else {
-                    const T num = fma_(o.a[p], x[p], fma_(o.b[p], py[r][p], S));
-                    const T rden =
-                        rcp_(add_(splat<T>(b.v[RowBuf<NS, HOMOG>::NA - 1][h][r]), o.ab[p]));
-                    const T pc = mul_(num, rden);
-                    if (MOM == 0) psi_put(psi_row, p, r, pc);
-                    if (ok) {
-                        if (SCHEME == 0) {
-                            x[p] = fma_(two, pc, neg_(x[p]));
-                            py[r][p] = fma_(two, pc, neg_(py[r][p]));
-                        } else {
-                            x[p] = pc;
-                            py[r][p] = pc;
-                        }
-                        acc0[r] = fma_(o.w[p], pc, acc0[r]);
-                        if (MOM == 3) {
-                            acc1[r] = fma_(o.wc[p], pc, acc1[r]);
-                            acc2[r] = fma_(o.ws[p], pc, acc2[r]);
-                        }
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int p = 0; p < N; ++p) xo[h][p] = x[p];
-        if constexpr (LATE) {
-#pragma unroll
-            for (int r = 0; r < kCols; ++r) out[0][h][r] = hsum(acc0[r]);
-            if constexpr (MOM == 3) {
-#pragma unroll
-                for (int r = 0; r < kCols; ++r) {
-                    out[MOM - 2][h][r] = hsum(acc1[r]);
-                    out[MOM - 1][h][r] = hsum(acc2[r]);
-                }
-            }
-        } else {
-            const RowAddr ra(A, blk, yneg, col0);
-            float v[kCols];
-#pragma unroll
-            for (int r = 0; r < kCols; ++r) v[r] = hsum(acc0[r]);
-            put8<MOM>(part_i + ra.base + h * ra.rs, v);
-            if constexpr (MOM == 0) {
-#pragma unroll
-                for (int k = 0; k < G; ++k) {
-                    const long long off = (long long)o.ord[k] * A.cells + ra.base + h * ra.rs;
-                    if (A.psi_split) st8_split(A.psi_split, off, psi_row[k]);
-                    else st8(A.psi + off, psi_row[k]);
-                }
-            }
-            if (MOM == 3) {
-#pragma unroll
-                for (int r = 0; r < kCols; ++r) v[r] = hsum(acc1[r]);
-                put8<MOM>(part_i + A.cells + ra.base + h * ra.rs, v);
-#pragma unroll
-                for (int r = 0; r < kCols; ++r) v[r] = hsum(acc2[r]);
-                put8<MOM>(part_i + 2 * A.cells + ra.base + h * ra.rs, v);
-            }
-        }
-    }
-}
-
-template <int G, int MOM, int SCHEME, bool HOMOG, bool XNEG>
-__device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &it,
-                                           const OrdPacks<G> &o)
-{
-    using T = typename Pack<G>::T;
-    constexpr int N = Pack<G>::N;
-    __shared__ T xbuf[2][kMaxWarps][kH][N];
-    const int g = threadIdx.x;
-    const int nwarps = blockDim.x >> 5;
-    const int L = (A.I + kCols - 1) / kCols;  // lanes that own cells
-    const bool lane_on = g < L;
-    const int d = XNEG ? (L - 1 - g) : g;     // lanes between this one and the inflow face
-    const int col0 = g * kCols;
-    const bool yneg = (it.quad >> 1) & 1;
-    const int nblk = (A.J + kH - 1) / kH;
-    const int T_steps = nblk + L - 1;
-    const bool full_cols = col0 + kCols <= A.I;
-
-    // incoming y-edge values of the lane's columns (face y_B, or y_T when s < 0)
-    T py[kCols][N];
-#pragma unroll
-    for (int r = 0; r < kCols; ++r)
-#pragma unroll
-        for (int k = 0; k < G; ++k) {
-            float v = 0.f;
-            if (A.inflow && lane_on && col0 + r < A.I && k < it.n)
-                v = A.inflow[(long long)o.ord[k] * A.inflow_stride + 2 * A.J + (yneg ? A.I : 0) +
-                             col0 + r];
-            setc(py[r][G == 1 ? 0 : k >> 1], G == 1 ? 0 : k & 1, v);
-        }
-
-    T xin[kH][N];
-#pragma unroll
-    for (int h = 0; h < kH; ++h)
-#pragma unroll
-        for (int p = 0; p < N; ++p) xin[h][p] = splat<T>(0.f);
-
-    constexpr int NS = n_src(MOM, G);
-    // source arrays of the item: the sample's moments, or (dense) one per ordinate
-    const float *srcp[NS];
-#pragma unroll
-    for (int m = 0; m < NS; ++m)
-        srcp[m] = MOM == 0 ? A.src + (long long)o.ord[m] * A.cells
-                           : A.src + ((long long)it.sample * MOM + m) * A.cells;
-    // moments: the sample's accumulator (dense mode) or the item's own partial array
-    float *part_i = A.part + (long long)(MOM == 0 ? it.sample : (int)blockIdx.x) *
-                                 n_out(MOM) * A.cells;
-
-    // The rows of the lane's block for step t + PD are loaded at the start of
-    // step t into a ring of PD + 1 register buffers indexed by t (the same index
-    // for every lane: lane d at step t works on block t - d).  With more than
-    // two arrays per cell (linear kernel) the registers are not there; the rows
-    // are then loaded at the start of their step.
-    constexpr int NA = RowBuf<NS, HOMOG>::NA;
-    constexpr bool PF = NA <= 2;
-    constexpr int PD = NA == 1 ? kPrefetch : (NA == 2 ? 1 : 0);
-    // moments are stored row by row inside the block (holding a whole block's
-    // moments until the end of the step measured slower on GB300)
-    constexpr bool STORE_LATE = false;
-    RowBuf<NS, HOMOG> buf[PD + 1];
-    auto step = [&](int t, RowBuf<NS, HOMOG> &cur, RowBuf<NS, HOMOG> &nxt) {
-        const int blk = t - d;
-        const bool active = lane_on && blk >= 0 && blk < nblk;
-        if (PF && lane_on && blk + PD >= 0 && blk + PD < nblk)
-            load_block<NS, HOMOG>(A, blk + PD, yneg, col0, srcp, nxt);
-        T xo[kH][N];
-        float out[STORE_LATE ? n_out(MOM) : 1][kH][kCols];
-        if (active) {
-            if (!PF) load_block<NS, HOMOG>(A, blk, yneg, col0, srcp, cur);
-            if (d == 0) {  // incoming x-edge values (face x_L, or x_R when c < 0)
-#pragma unroll
-                for (int h = 0; h < kH; ++h)
-#pragma unroll
-                    for (int k = 0; k < G; ++k) {
-                        const int jl = blk * kH + h;
-                        float v = 0.f;
-                        if (A.inflow && jl < A.J && k < it.n) {
-                            const int j = yneg ? (A.J - 1 - jl) : jl;
-                            v = A.inflow[(long long)o.ord[k] * A.inflow_stride + (XNEG ? A.J : 0) +
-                                         j];
-                        }
-                        setc(xin[h][G == 1 ? 0 : k >> 1], G == 1 ? 0 : k & 1, v);
-                    }
-            }
-            const bool full = full_cols && (blk + 1) * kH <= A.J;
-            if (full)
-                sweep_block<G, MOM, SCHEME, HOMOG, XNEG, false, STORE_LATE>(
-                    A, blk, yneg, col0, o, py, xin, xo, cur, out, part_i);
-            else
-                sweep_block<G, MOM, SCHEME, HOMOG, XNEG, true, STORE_LATE>(
-                    A, blk, yneg, col0, o, py, xin, xo, cur, out, part_i);
-        } else {
-#pragma unroll
-            for (int h = 0; h < kH; ++h)
-#pragma unroll
-                for (int p = 0; p < N; ++p) xo[h][p] = splat<T>(0.f);
-        }
-        // hand the outgoing x-edge values to the downstream lane
-#pragma unroll
-        for (int h = 0; h < kH; ++h)
-#pragma unroll
-            for (int p = 0; p < N; ++p) xin[h][p] = shfl1<XNEG>(xo[h][p]);
-        // the step's moments to global memory (when not stored row by row)
-        if (STORE_LATE && active) {
-            const RowAddr ra(A, blk, yneg, col0);
-#pragma unroll
-            for (int h = 0; h < kH; ++h)
-                if (blk * kH + h < A.J)
-#pragma unroll
-                    for (int m = 0; m < (STORE_LATE ? n_out(MOM) : 1); ++m)
-                        put8<MOM>(part_i + m * A.cells + ra.base + h * ra.rs, out[m][h]);
-        }
-        if (nwarps > 1) {
-            const int lane = g & 31, w = g >> 5;
-            const bool sender = XNEG ? (lane == 0 && w > 0) : (lane == 31 && w + 1 < nwarps);
-            if (sender) {
-#pragma unroll
-                for (int h = 0; h < kH; ++h)
-#pragma unroll
-                    for (int p = 0; p < N; ++p) xbuf[t & 1][w][h][p] = xo[h][p];
-            }
-            __syncthreads();
-            const bool recv = XNEG ? (lane == 31 && w + 1 < nwarps) : (lane == 0 && w > 0);
-            if (recv) {
-                const int src_w = XNEG ? w + 1 : w - 1;
-#pragma unroll
-                for (int h = 0; h < kH; ++h)
-#pragma unroll
-                    for (int p = 0; p < N; ++p) xin[h][p] = xbuf[t & 1][src_w][h][p];
-            }
-        }
-    };
-    if constexpr (PF) {
-        // blocks of steps 0 .. PD-1 (buffer k holds the block of step k)
-#pragma unroll
-        for (int k = 0; k < PD; ++k)
-            if (lane_on && k - d >= 0 && k - d < nblk)
-                load_block<NS, HOMOG>(A, k - d, yneg, col0, srcp, buf[k]);
-        int t = 0;
-        for (; t + PD < T_steps; t += PD + 1) {
-#pragma unroll
-            for (int k = 0; k <= PD; ++k) step(t + k, buf[k], buf[(k + PD) % (PD + 1)]);
-        }
-#pragma unroll
-        for (int k = 0; k < PD; ++k)
-            if (t + k < T_steps) step(t + k, buf[k], buf[(k + PD) % (PD + 1)]);
-    } else {
-        for (int t = 0; t < T_steps; ++t) step(t, buf[0], buf[0]);
-    }
-}
-
-template <int G, int MOM, int SCHEME, bool HOMOG>
-__global__ void __launch_bounds__(32 * kMaxWarps) sweep2d_kernel(const SweepArgs A)
-{
-    const SweepItem it = A.items[blockIdx.x];
-    if (!A.active[it.sample]) return;
-    OrdPacks<G> o;
-    const float f = SCHEME == 0 ? 2.f : 1.f;
-#pragma unroll
-    for (int k = 0; k < G; ++k) {
-        float c = 0.f, s = 0.f, w = 0.f;
-        int ord = 0;
-        if (k < it.n) {
-            ord = it.ord[k];
-            c = A.oc[ord];
-            s = A.os[ord];
-            w = A.ow[ord];
-        }
-        o.ord[k] = ord;
-        const float a = f * fabsf(c) * A.inv_dx, b = f * fabsf(s) * A.inv_dy;
-        const int p = G == 1 ? 0 : k >> 1, i = G == 1 ? 0 : k & 1;
-        setc(o.a[p], i, a);
-        setc(o.b[p], i, b);
-        setc(o.ab[p], i, a + b);
-        setc(o.w[p], i, w);
-        setc(o.rd[p], i, HOMOG ? 1.f / (A.sigma_t_homog + a + b) : 0.f);
-        setc(o.c[p], i, c);
-        setc(o.s[p], i, s);
-        setc(o.wc[p], i, w * c);
-        setc(o.ws[p], i, w * s);
-        const float rd = 1.f / (A.sigma_t_homog + a + b);
-        setc(o.al[p], i, (a - b - A.sigma_t_homog) * rd);
-        setc(o.a2[p], i, 2.f * a * rd);
-        setc(o.b2[p], i, 2.f * b * rd);
-        setc(o.be[p], i, (b - a - A.sigma_t_homog) * rd);
-        setc(o.r2[p], i, 2.f * rd);
-        setc(o.wh[p], i, 0.5f * w);
-        setc(o.ar[p], i, a * rd);
-        setc(o.br[p], i, b * rd);
-    }
-    if (it.quad & 1)
-        sweep_item<G, MOM, SCHEME, HOMOG, true>(A, it, o);
-    else
-        sweep_item<G, MOM, SCHEME, HOMOG, false>(A, it, o);
-}
-
-template <int G, int MOM>
-cudaError_t launch_g(const SweepArgs &a, int n_items, int nwarps, int scheme, bool homog,
-                     cudaStream_t st)
-{
-    const dim3 grid(n_items), block(32 * nwarps);
-    if (scheme == 0) {
-        if (homog) sweep2d_kernel<G, MOM, 0, true><<<grid, block, 0, st>>>(a);
-        else sweep2d_kernel<G, MOM, 0, false><<<grid, block, 0, st>>>(a);
-    } else {
-        if (homog) sweep2d_kernel<G, MOM, 1, true><<<grid, block, 0, st>>>(a);
-        else sweep2d_kernel<G, MOM, 1, false><<<grid, block, 0, st>>>(a);
-    }
-    return cudaGetLastError();
-}
-
-}  // namespace
 
 cudaError_t launch_sweep2d(const SweepArgs &a, int n_items, int nwarps, int G, int scheme,
-                           bool homog, int mom, cudaStream_t st)
+                           bool homog, int mom, int rows, cudaStream_t st)
 {
-    if (n_items <= 0) return cudaSuccess;
-    if (nwarps < 1 || nwarps > kMaxWarps) return cudaErrorInvalidValue;
-    if (mom == 1) {
-        if (G == 1) return launch_g<1, 1>(a, n_items, nwarps, scheme, homog, st);
-        if (G == 2) return launch_g<2, 1>(a, n_items, nwarps, scheme, homog, st);
-        if (G == 4) return launch_g<4, 1>(a, n_items, nwarps, scheme, homog, st);
-    } else if (mom == 3) {
-        if (G == 1) return launch_g<1, 3>(a, n_items, nwarps, scheme, homog, st);
-        if (G == 2) return launch_g<2, 3>(a, n_items, nwarps, scheme, homog, st);
-        if (G == 4) return launch_g<4, 3>(a, n_items, nwarps, scheme, homog, st);
-    } else if (mom == 0) {
-        if (G == 1) return launch_g<1, 0>(a, n_items, nwarps, scheme, homog, st);
-        if (G == 2) return launch_g<2, 0>(a, n_items, nwarps, scheme, homog, st);
-        if (G == 4) return launch_g<4, 0>(a, n_items, nwarps, scheme, homog, st);
-    }
-    return cudaErrorInvalidValue;
+    if (rows == 2) return launch_sweep2d_rows2(a, n_items, nwarps, G, scheme, homog, mom, st);
+    if (rows != 4) return cudaErrorInvalidValue;
+    return launch_rows(a, n_items, nwarps, G, scheme, homog, mom, st);
 }
 
 }  // namespace romk

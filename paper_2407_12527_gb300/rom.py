@@ -33,7 +33,8 @@ class rom_options(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
                 ("fixed_iters", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("tile_g", ctypes.c_int), ("time_kernels", ctypes.c_int),
-                ("dense_source", ctypes.c_int), ("dense_precision", ctypes.c_int)]
+                ("dense_source", ctypes.c_int), ("dense_precision", ctypes.c_int),
+                ("rows_per_step", ctypes.c_int)]
 
 
 class rom_stats(ctypes.Structure):
@@ -43,7 +44,7 @@ class rom_stats(ctypes.Structure):
                 ("gpu_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("sweep_ms", ctypes.c_double), ("sweep_launches", ctypes.c_int64),
                 ("source_ms", ctypes.c_double), ("source_launches", ctypes.c_int64),
-                ("tile_g", ctypes.c_int)]
+                ("tile_g", ctypes.c_int), ("rows_per_step", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -102,7 +102,9 @@ GRIDS = [
 @pytest.mark.parametrize("scheme", ["dd", "step"])
 @pytest.mark.parametrize("grid", GRIDS, ids=[f"{g[0]}x{g[1]}" for g in GRIDS])
 @pytest.mark.parametrize("homog", [True, False])
-def test_fixed_k_parity_random_directions(rom, scheme, grid, homog):
+@pytest.mark.parametrize("rows", [4, 2])
+def test_fixed_k_parity_random_directions(rom, scheme, grid, homog, rows):
+    """Rows = grid rows a lane advances per wavefront step (both kernel shapes)."""
     I, J, bounds = grid
     st, ss, q = W.random_medium(I, J, seed=I * 31 + J)
     if homog:
@@ -112,27 +114,33 @@ def test_fixed_k_parity_random_directions(rom, scheme, grid, homog):
             for M in (5, 12, 3)]
     K = 4
     gpu = gpu_solve(rom, I, J, bounds, st, ss, q, sets=sets, scheme=rom.SCHEME[scheme],
-                    fixed_iters=K)
+                    fixed_iters=K, rows_per_step=rows)
     ref = O.solve_xy(I, J, bounds, st, ss, q, sets, scheme=scheme, fixed_iters=K)
     for k in range(len(sets)):
         assert rel(gpu["phi"][k], ref["phi"][k]) < TOL, k
     assert list(gpu["iters"]) == [K] * len(sets)
+    assert gpu["stats"]["rows_per_step"] == rows
 
 
 @pytest.mark.parametrize("tile_g", [-1, 1, 2, 4])
-def test_work_item_size_does_not_change_results(rom, tile_g):
+@pytest.mark.parametrize("rows", [0, 2, 4])
+def test_work_item_size_does_not_change_results(rom, tile_g, rows):
     I, J = 70, 45
     bounds = (0, 1, 0, 1)
     st, ss, q = W.random_medium(I, J, seed=3)
     nz, nt = [2, 3, 1], [2, 3, 5]
     gpu = gpu_solve(rom, I, J, bounds, st, ss, q, seed=77, nz=nz, nt=nt, fixed_iters=5,
-                    tile_g=tile_g)
+                    tile_g=tile_g, rows_per_step=rows)
     sets = [O.rom_ordinates_xy(77, k, nz[k], nt[k]) for k in range(3)]
     ref = O.solve_xy(I, J, bounds, st, ss, q, sets, fixed_iters=5)
     for k in range(3):
         assert rel(gpu["phi"][k], ref["phi"][k]) < TOL
     assert gpu["stats"]["tile_g"] == (tile_g if tile_g > 0 else gpu["stats"]["tile_g"])
     assert gpu["stats"]["tile_g"] in (1, 2, 4)
+    assert gpu["stats"]["rows_per_step"] == (rows if rows else
+                                             (gpu["stats"]["rows_per_step"] if tile_g == -1
+                                              else 4))
+    assert gpu["stats"]["rows_per_step"] in (2, 4)
 
 
 # ------------------------------------------------------ converged parity
@@ -170,13 +178,14 @@ def test_dom_uniform_and_gauss_parity(rom):
         assert rel(phi, ref["phi"][0]) < TOL, kind
 
 
-def test_linear_kernel_parity(rom):
+@pytest.mark.parametrize("rows", [4, 2])
+def test_linear_kernel_parity(rom, rows):
     """Linear anisotropic kernel g = 0.9 (eq. anisotropic kernel): the GPU's
     3-moment source against the oracle's dense w_l' P(u_l', u_l) contraction."""
     p = W.example_2_1(I=48, J=40, g=0.9)
     nz, nt = [2, 3], [2, 3]
     gpu = gpu_solve(rom, p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, seed=9, nz=nz, nt=nt,
-                    kernel="linear", g=0.9, fixed_iters=8)
+                    kernel="linear", g=0.9, fixed_iters=8, rows_per_step=rows)
     sets = [O.rom_ordinates_xy(9, k, nz[k], nt[k]) for k in range(2)]
     ref = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, sets, kernel="linear", g=0.9,
                      fixed_iters=8)
@@ -274,6 +283,9 @@ def test_invalid_arguments_rejected(rom):
     assert e.value.code == -1
     with pytest.raises(rom.RomError) as e:
         ctx.set_grid(4, 4, (0, 1, 0, 1), 1.0, 0.5, 1.0) or ctx.set_options(dense_source=2)
+    assert e.value.code == -1
+    with pytest.raises(rom.RomError) as e:
+        ctx.set_options(rows_per_step=3)
     assert e.value.code == -1
     ctx.close()
 
