@@ -465,8 +465,8 @@ def run_ours(args):
     # DRAM bytes of one full launch from the committed ncu captures, used only
     # while the kernel source is the one that was captured
     traffic = None
-    if WL.name == "point_source" and s["tile_g"] == 2:
-        traffic = traffic_record("sweep2d_point_source_256", "sweep2d.cu", WL.samples)
+    if WL.name == "point_source" and s["tile_g"] == 2 and s["rows_per_step"] == 4:
+        traffic = traffic_record("sweep2d_point_source_256", "sweep2d_impl.cuh", WL.samples)
     elif WL.name == "lognormal_cube" and s["tile_g"] == 2:
         traffic = traffic_record("sweep3d_lognormal_cube_128", "sweep3d.cu", WL.samples)
     if tc and src_ms > 0:
@@ -488,9 +488,12 @@ def run_ours(args):
             sw = sweep_upd * DENSE_SWEEP_BYTES_PER_UPDATE / (sweep_ms / 1e3) / 1e9
             secondary = dict(roofline)
             roofline = {"bound": "hbm", "achieved": sw, "peak": hbm_peak, "unit": "GB/s",
-                        "frac": sw / hbm_peak, "traffic": None,
-                        "traffic_note": "no ncu capture of the dense-mode sweep; achieved counts "
-                                        "the algorithmic bytes, 8 B per cell-ordinate update",
+                        "frac": sw / hbm_peak,
+                        "traffic": traffic_record("sweep2d_dense_hg_disc_512",
+                                                  "sweep2d_impl.cuh", WL.samples),
+                        "traffic_note": "DRAM read+write bytes of one launch with every sample "
+                                        "active (ncu, scaled by samples); achieved counts the "
+                                        "algorithmic bytes, 8 B per cell-ordinate update",
                         "kernel": "sweep2d_kernel (K1, dense mode: per-ordinate sources in, "
                                   "split-BF16 psi out)",
                         "launches": sweep_n, "avg_launch_us": 1e3 * sweep_ms / max(sweep_n, 1),
