@@ -29,10 +29,10 @@
  *     error inside a call is reported as ROM_ERR_CUDA and leaves the context
  *     in need of rom_destroy.
  *   - Arithmetic: sweeps and source updates in FP32, the source-iteration
- *     residual norms and the sample average in FP64.  3D sweeps add each
- *     ordinate's contribution to the scalar flux with atomic FP32 vector
- *     additions, so the order of the terms, and the last bits of phi, can
- *     differ from run to run.
+ *     residual norms and the sample average in FP64.  Sweeps add each work
+ *     item's (one to four ordinates') contribution to its sample's flux
+ *     moments with atomic FP32 vector additions, so the order of the terms,
+ *     and the last bits of phi, can differ from run to run.
  */
 #ifndef ROM_GB300_H
 #define ROM_GB300_H
@@ -271,8 +271,8 @@ const char *rom_version(void);
  * application owns all device memory through its own pool, and latency-bound
  * paths where an allocation (and the synchronisation it can imply) is not
  * allowed.  The context API allocates its buffers with cudaMalloc; this call
- * instead keeps its scratch (padded copies of the inputs and the per-work-item
- * moment partials) in one array of ROM_NOALLOC_SCRATCH_BYTES that the library
+ * instead keeps its scratch (padded copies of the inputs and the per-sample
+ * moment accumulators) in one array of ROM_NOALLOC_SCRATCH_BYTES that the library
  * places in device memory when it is loaded.  Every GPU that loads the
  * library holds that array until the process exits.
  *
@@ -291,8 +291,8 @@ const char *rom_version(void);
  * vectors) and weights (host FP64 [sum M], > 0) give the ordinate sets, as in
  * rom_set_ordinates.  errbuf (may be NULL) receives a message on failure.
  * Limits: I <= 2048, n_samples <= 1024, sum M <= 8192, and the scratch the
- * problem needs (about 4 J ceil(I/8)*8 bytes times 1 + n_samples + the number of
- * work items, two ordinates of one quadrant per item) must fit in
+ * problem needs (about 4 J ceil(I/8)*8 bytes times 1 + 2 n_samples, plus small
+ * tables) must fit in
  * ROM_NOALLOC_SCRATCH_BYTES; larger problems return ROM_ERR_INVALID_ARG with
  * the needed size in errbuf.  No cudaMalloc, cudaFree or other allocating
  * routine is called.
@@ -302,7 +302,9 @@ const char *rom_version(void);
  * call before any stream capture.  The call returns after enqueueing the work;
  * phi is ready when the stream reaches that point.  All calls on a device share
  * the one scratch array, which keeps the last call's contents; no part of it
- * needs to start at zero, because every call writes each byte it reads.  Calls
+ * needs to start at zero, because every call writes (or clears) each byte it
+ * reads.  The work items of a sample add their moments to one accumulator, so
+ * the last bits of phi depend on the order of those additions.  Calls
  * whose work overlaps on the GPU (other streams or host threads) race on the
  * array: serialise them.
  */

@@ -6,8 +6,8 @@
 // owns all device memory through its own pool, or real-time code paths where
 // an allocation (and the implicit synchronisation it may bring) is not
 // allowed.  For them this entry point runs the sweep kernel of the library with
-// its scratch memory -- padded copies of the inputs and the per-work-item
-// moment partials -- placed in one fixed-size array in the library's own
+// its scratch memory -- padded copies of the inputs and the per-sample moment
+// accumulators -- placed in one fixed-size array in the library's own
 // device memory instead of in buffers it would allocate.
 //
 // The array below is a file-scope __device__ variable: every GPU that loads
@@ -19,8 +19,8 @@
 // set-up, make the first call on each device before any stream capture.
 //
 // All calls on a device share the array and it keeps the contents of the last
-// call.  Nothing in it has to start at zero: every call overwrites each byte it
-// later reads.  Calls whose work overlaps on the GPU (different streams, or
+// call.  Nothing in it has to start at zero: every call overwrites (or clears)
+// each byte it later reads.  Calls whose work overlaps on the GPU (different streams, or
 // different host threads) race on the array and give wrong results; serialise
 // them.
 #include <cuda_runtime.h>
@@ -51,7 +51,6 @@ void *g_scratch_addr[kMaxDevices];
 // Host staging of the small tables (guarded by g_mu; copied before return).
 struct HostTables {
     romk::SweepItem items[kMaxItems];
-    int item_begin[kMaxSamples + 1];
     int active[kMaxSamples];
     float c[kMaxOrdinates], s[kMaxOrdinates], w[kMaxOrdinates];
 };
@@ -80,9 +79,8 @@ __global__ void noalloc_pad_kernel(const float *sigma_t, const float *src, int S
     }
 }
 
-// phi[s][j][i] = sum over the work items of sample s (in item order) of their partials.
-__global__ void noalloc_sum_kernel(const float *part, const int *item_begin, int S, int I, int J,
-                                   int NXP, float *phi)
+// phi[s][j][i] = the moments the work items of sample s added to its accumulator.
+__global__ void noalloc_unpad_kernel(const float *part, int S, int I, int J, int NXP, float *phi)
 {
     const long long cells = (long long)J * NXP;
     const long long n = (long long)S * J * I;
@@ -90,10 +88,7 @@ __global__ void noalloc_sum_kernel(const float *part, const int *item_begin, int
          v += (long long)gridDim.x * blockDim.x) {
         const long long s = v / ((long long)J * I), r = v - s * J * I;
         const long long j = r / I, i = r - j * I;
-        float acc = 0.f;
-        for (int it = item_begin[s]; it < item_begin[s + 1]; ++it)
-            acc += part[(long long)it * cells + j * NXP + i];
-        phi[v] = acc;
+        phi[v] = part[s * cells + j * NXP + i];
     }
 }
 
@@ -141,7 +136,6 @@ extern "C" int rom_sweep_xy_noalloc(void *cuda_stream, int I, int J, double dx, 
     int n_items = 0;
     long long off = 0;
     for (int s = 0; s < n_samples; ++s) {
-        g_host.item_begin[s] = n_items;
         g_host.active[s] = 1;
         for (int code = 0; code < 4; ++code) {
             romk::SweepItem cur{};
@@ -171,7 +165,6 @@ extern "C" int rom_sweep_xy_noalloc(void *cuda_stream, int I, int J, double dx, 
         }
         off += m_per_sample[s];
     }
-    g_host.item_begin[n_samples] = n_items;
     for (long long o = 0; o < mtot; ++o) {
         g_host.c[o] = (float)dirs[3 * o];
         g_host.s[o] = (float)dirs[3 * o + 1];
@@ -184,9 +177,8 @@ extern "C" int rom_sweep_xy_noalloc(void *cuda_stream, int I, int J, double dx, 
     size_t o_st = 0;
     size_t o_src = o_st + align256(cells * 4);
     size_t o_part = o_src + align256((size_t)n_samples * cells * 4);
-    size_t o_items = o_part + align256((size_t)n_items * cells * 4);
-    size_t o_begin = o_items + align256((size_t)n_items * sizeof(romk::SweepItem));
-    size_t o_active = o_begin + align256((size_t)(n_samples + 1) * sizeof(int));
+    size_t o_items = o_part + align256((size_t)n_samples * cells * 4);
+    size_t o_active = o_items + align256((size_t)n_items * sizeof(romk::SweepItem));
     size_t o_c = o_active + align256((size_t)n_samples * sizeof(int));
     size_t o_s = o_c + align256((size_t)mtot * 4);
     size_t o_w = o_s + align256((size_t)mtot * 4);
@@ -223,8 +215,6 @@ extern "C" int rom_sweep_xy_noalloc(void *cuda_stream, int I, int J, double dx, 
 
     NA_CK(cudaMemcpyAsync(base + o_items, g_host.items, n_items * sizeof(romk::SweepItem),
                           cudaMemcpyHostToDevice, st));
-    NA_CK(cudaMemcpyAsync(base + o_begin, g_host.item_begin, (n_samples + 1) * sizeof(int),
-                          cudaMemcpyHostToDevice, st));
     NA_CK(cudaMemcpyAsync(base + o_active, g_host.active, n_samples * sizeof(int),
                           cudaMemcpyHostToDevice, st));
     NA_CK(cudaMemcpyAsync(base + o_c, g_host.c, mtot * 4, cudaMemcpyHostToDevice, st));
@@ -233,6 +223,7 @@ extern "C" int rom_sweep_xy_noalloc(void *cuda_stream, int I, int J, double dx, 
 
     float *st_pad = (float *)(base + o_st), *src_pad = (float *)(base + o_src);
     float *part = (float *)(base + o_part);
+    NA_CK(cudaMemsetAsync(part, 0, (size_t)n_samples * cells * 4, st));  // the sweep adds into it
     noalloc_pad_kernel<<<blocks((long long)(n_samples + 1) * cells), 256, 0, st>>>(
         sigma_t, src, n_samples, I, J, NXP, st_pad, src_pad);
     NA_CK(cudaGetLastError());
@@ -257,8 +248,8 @@ extern "C" int rom_sweep_xy_noalloc(void *cuda_stream, int I, int J, double dx, 
     a.cells = (long long)cells;
     const int L = (I + romk::kCols - 1) / romk::kCols;
     NA_CK(romk::launch_sweep2d(a, n_items, (L + 31) / 32, kG, scheme, false, 1, 4, st));
-    noalloc_sum_kernel<<<blocks((long long)n_samples * J * I), 256, 0, st>>>(
-        part, (const int *)(base + o_begin), n_samples, I, J, NXP, phi);
+    noalloc_unpad_kernel<<<blocks((long long)n_samples * J * I), 256, 0, st>>>(part, n_samples, I,
+                                                                               J, NXP, phi);
     NA_CK(cudaGetLastError());
 #undef NA_CK
     return ROM_OK;

@@ -1,8 +1,8 @@
 // reduce.cu -- scattering-source update, source-iteration residual and sample
 // average (K2, K5, K6) plus small data-movement kernels.
 //
-// combine:  phi_s = sum over the work items of sample s of their moments
-//           (fixed item order, FP32), the new source moments
+// combine:  phi_s = the moments the work items of sample s added to its
+//           accumulator during the sweep (read and cleared), the new source moments
 //             isotropic: S = sigma_S phi + q                       (P = 1)
 //             linear:    S0 = sigma_S phi + q, S1 = g sigma_S (Jx, Jy)
 //           so that the next sweep forms S_l = S0 + c_l S1x + s_l S1y
@@ -40,7 +40,6 @@ __global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
 {
     const int s = blockIdx.y;
     if (!A.active[s]) return;
-    const int ib = A.item_begin[s], ie = A.item_begin[s + 1];
     const long long cells = A.cells;  // a multiple of 8: every thread owns one 32-byte sector
     float *phi = A.phi + (long long)s * MOM * cells;
     float *src = A.src + (long long)s * MOM * cells;
@@ -48,58 +47,21 @@ __global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
     for (long long v = 8 * ((long long)blockIdx.x * blockDim.x + threadIdx.x); v < cells;
          v += 8LL * gridDim.x * blockDim.x) {
         float acc[MOM][8];
-#pragma unroll
-        for (int m = 0; m < MOM; ++m)
-#pragma unroll
-            for (int e = 0; e < 8; ++e) acc[m][e] = 0.f;
         float old[8], ss[8], qq[8], out[8];
         ld8_volatile(phi + v, old);
         ldg8(A.sigma_s + v, ss);
         ldg8(A.q + v, qq);
-        int it = ib;
-        if (A.zero_part) {  // the sample's accumulated moments, cleared for the next sweep
+        {  // the sample's accumulated moments, cleared for the next sweep
             float zero[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) zero[e] = 0.f;
 #pragma unroll
             for (int m = 0; m < MOM; ++m) {
-                float *p = const_cast<float *>(A.part) + ((long long)s * MOM + m) * cells + v;
+                float *p = A.acc + ((long long)s * MOM + m) * cells + v;
                 ld8_volatile(p, acc[m]);
                 stg8(p, zero);
             }
-            it = ie;
         }
-        // items in batches of eight independent loads, summed in item order
-        for (; it + 8 <= ie; it += 8)
-#pragma unroll
-            for (int m = 0; m < MOM; ++m) {
-                float t[8][8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) ldg8(A.part + ((long long)(it + u) * MOM + m) * cells + v, t[u]);
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) acc[m][e] += t[u][e];
-            }
-        for (; it + 4 <= ie; it += 4)
-#pragma unroll
-            for (int m = 0; m < MOM; ++m) {
-                float t[4][8];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) ldg8(A.part + ((long long)(it + u) * MOM + m) * cells + v, t[u]);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) acc[m][e] += t[u][e];
-            }
-        for (; it < ie; ++it)
-#pragma unroll
-            for (int m = 0; m < MOM; ++m) {
-                float t[8];
-                ldg8(A.part + ((long long)it * MOM + m) * cells + v, t);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) acc[m][e] += t[e];
-            }
         // per-element squares in FP32 (a few terms per thread), norms in FP64 below
 #pragma unroll
         for (int e = 0; e < 8; ++e) {

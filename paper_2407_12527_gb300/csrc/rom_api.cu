@@ -91,8 +91,7 @@ struct rom_ctx {
     int tuned_g = 0;  // measured choice (tile_g = -1), valid while the layout is unchanged
     int tuned_h = 0;  // rows per step of that choice
     std::vector<SweepItem> items;
-    std::vector<int> item_begin;
-    DevBuf items_dev, item_begin_dev;
+    DevBuf items_dev;
     // 3D: CTA item lists (one octant each) and the tile hand-off buffers
     std::vector<int> cta_begin, cta_list;
     DevBuf cta_begin_dev, cta_list_dev, xface, yface, err3;
@@ -290,13 +289,12 @@ void set_homog(rom_ctx *ctx, bool homog, float sigma_t)
 }
 
 // 1: isotropic moment, 3: linear-kernel moments, 0: dense operator
-// The sweep adds each sample's moments to one accumulator (vector atomics; the
-// combine reads and clears it) instead of storing per-item partials that the
-// combine sums in item order: in 3D (per-item partials would be cells x
-// ordinates) and with the dense operator (many items per sample, partials of
-// GB size).  The moment modes in X-Y keep the per-item partials: few items per
-// sample, bitwise reproducible sums, and faster there.
-bool accumulates(const rom_ctx *ctx) { return ctx->dim == 3 || ctx->MOM == 0; }
+// The sweep adds each sample's moments to one accumulator (vector reductions in
+// L2; the combine reads and clears it) rather than storing per-item partials for
+// the combine to sum: per-item partials would be cells x ordinates in 3D and GB
+// in the dense mode, and in the X-Y moment modes the accumulator measured 19%
+// faster per source iteration (the sweep writes less, the combine reads one
+// array).  The price is the order of the additions, which follows the timing.
 // 3D keeps its accumulators (and source, sigma_T) in diagonal storage, not in part
 bool uses_part(const rom_ctx *ctx) { return ctx->dim == 2; }
 
@@ -344,10 +342,8 @@ int build_items3(rom_ctx *ctx)
     const int G = ctx->opt.tile_g == 1 ? 1 : 2;
     ctx->G_used = G;
     ctx->items.clear();
-    ctx->item_begin.resize(ctx->S + 1);
     std::vector<int> byo[8];
     for (int s = 0; s < ctx->S; ++s) {
-        ctx->item_begin[s] = s;  // the combine reads one accumulated array per sample
         std::vector<int> ords[8];
         for (int l = 0; l < ctx->M[s]; ++l) {
             const long long o = ctx->off[s] + l;
@@ -375,7 +371,6 @@ int build_items3(rom_ctx *ctx)
                 ctx->items.push_back(it);
             }
     }
-    ctx->item_begin[ctx->S] = ctx->S;
     const long long total = (long long)ctx->items.size();
     const int L = (ctx->I + romk::kCols - 1) / romk::kCols;
     const int strips = romk::sweep3d_tile_cols() / romk::kCols;
@@ -399,7 +394,6 @@ int build_items3(rom_ctx *ctx)
     ctx->n_ctas3 = (int)ctx->cta_begin.size() - 1;
     int rc;
     if ((rc = ensure(ctx, ctx->items_dev, ctx->items.size() * sizeof(SweepItem))) ||
-        (rc = ensure(ctx, ctx->item_begin_dev, ctx->item_begin.size() * sizeof(int))) ||
         (rc = ensure(ctx, ctx->cta_begin_dev, ctx->cta_begin.size() * sizeof(int))) ||
         (rc = ensure(ctx, ctx->cta_list_dev, ctx->cta_list.size() * sizeof(int))) ||
         (rc = ensure(ctx, ctx->err3, sizeof(int))))
@@ -413,8 +407,6 @@ int build_items3(rom_ctx *ctx)
     if (!ctx->items.empty())
         CK(cudaMemcpyAsync(ctx->items_dev.p, ctx->items.data(), ctx->items.size() * sizeof(SweepItem),
                            cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->item_begin_dev.p, ctx->item_begin.data(),
-                       ctx->item_begin.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->cta_begin_dev.p, ctx->cta_begin.data(),
                        ctx->cta_begin.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     if (!ctx->cta_list.empty())
@@ -432,10 +424,8 @@ int build_items(rom_ctx *ctx)
     ctx->G_used = G;
     ctx->H_used = choose_rows(ctx);
     ctx->items.clear();
-    ctx->item_begin.assign(ctx->S + 1, 0);
     std::vector<int> byq[4];
     for (int s = 0; s < ctx->S; ++s) {
-        ctx->item_begin[s] = (int)ctx->items.size();
         for (int qd = 0; qd < 4; ++qd) byq[qd].clear();
         if (ctx->ord_source == ORD_SEED) {
             const int nblk = ctx->seed_octants ? 8 : 4;
@@ -466,16 +456,11 @@ int build_items(rom_ctx *ctx)
             }
         }
     }
-    ctx->item_begin[ctx->S] = (int)ctx->items.size();
     int rc;
-    if ((rc = ensure(ctx, ctx->items_dev, ctx->items.size() * sizeof(SweepItem))) ||
-        (rc = ensure(ctx, ctx->item_begin_dev, ctx->item_begin.size() * sizeof(int))))
-        return rc;
+    if ((rc = ensure(ctx, ctx->items_dev, ctx->items.size() * sizeof(SweepItem)))) return rc;
     if (!ctx->items.empty())
         CK(cudaMemcpyAsync(ctx->items_dev.p, ctx->items.data(), ctx->items.size() * sizeof(SweepItem),
                            cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->item_begin_dev.p, ctx->item_begin.data(),
-                       ctx->item_begin.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));  // host vectors may change before the next use
     ctx->items_dirty = false;
     return ROM_OK;
@@ -733,13 +718,11 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     romk::CombineArgs ca{};
     ca.S = ctx->S;
     ca.MOM = ctx->MOM == 0 ? 1 : ctx->MOM;
-    ca.zero_part = accumulates(ctx) ? 1 : 0;
     ca.chunks = ctx->chunks;
     ca.cells = padded_cells(ctx);
     ca.cells4 = ca.cells / 4;
     ca.g = (float)ctx->g;
-    ca.part = (const float *)ctx->part.p;
-    ca.item_begin = (const int *)ctx->item_begin_dev.p;
+    ca.acc = (float *)ctx->part.p;
     ca.phi = (float *)ctx->phi.p;
     ca.src = (float *)ctx->src.p;
     ca.sigma_s = (const float *)ctx->sigs.p;
@@ -816,8 +799,7 @@ int autotune_g(rom_ctx *ctx)
         if (G > cap || (want_h != 0 && H != want_h)) continue;
         ctx->opt.tile_g = G;
         if ((rc = build_items(ctx))) return rc;
-        const size_t units = accumulates(ctx) ? (size_t)ctx->S : ctx->items.size();
-        if ((rc = ensure(ctx, ctx->part, units * MOMk * cells * sizeof(float))))
+        if ((rc = ensure(ctx, ctx->part, (size_t)ctx->S * MOMk * cells * sizeof(float))))
             return rc;
         CK(romk::launch_init_state(ctx->S, MOMk, cells, (const float *)ctx->q.p,
                                    (float *)ctx->phi.p, (float *)ctx->src.p, (int *)ctx->active.p,
@@ -944,7 +926,7 @@ void rom_destroy(rom_ctx *ctx)
     invalidate_graph(ctx);
     DevBuf *bufs[] = {&ctx->sigt, &ctx->sigs, &ctx->q, &ctx->inflow_dev, &ctx->c64, &ctx->s64,
                       &ctx->z64, &ctx->w64, &ctx->c32, &ctx->s32, &ctx->w32, &ctx->items_dev,
-                      &ctx->item_begin_dev, &ctx->phi, &ctx->src, &ctx->part, &ctx->partials,
+                      &ctx->phi, &ctx->src, &ctx->part, &ctx->partials,
                       &ctx->active, &ctx->iters, &ctx->flags, &ctx->resid, &ctx->n_active,
                       &ctx->avg, &ctx->sum, &ctx->tmp, &ctx->psi, &ctx->src_ord, &ctx->Amat,
                       &ctx->dtab, &ctx->z32, &ctx->cta_begin_dev, &ctx->cta_list_dev,
@@ -1435,10 +1417,8 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
                                        : (size_t)ctx->S * MOM * cells * sizeof(float);
     const size_t src_bytes = ctx->dim == 3 ? 0 : state;
     const size_t nI = (size_t)n_cells(ctx);
-    // part: the moments of each sample accumulated by the sweep, or of each work item
-    const size_t part_units = !uses_part(ctx)   ? 0
-                              : accumulates(ctx) ? (size_t)ctx->S
-                                                 : ctx->items.size();
+    // part: the moments of each sample, accumulated by the sweep (X-Y)
+    const size_t part_units = uses_part(ctx) ? (size_t)ctx->S : 0;
     if (ctx->dim == 3) {
         const romk::Skew3 sk = romk::make_skew3(ctx->J, ctx->K, ctx->NXP);
         if (sk.cells >= (1LL << 31))
@@ -1483,7 +1463,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     if (ctx->MOM == 0 && ctx->opt.dense_precision == 1)
         CK(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), ctx->stream));
-    if (uses_part(ctx) && accumulates(ctx))  // the sweep accumulates; the combine clears it
+    if (uses_part(ctx))  // the sweep accumulates; the combine clears it
         CK(cudaMemsetAsync(ctx->part.p, 0, part_units * MOM * cells * sizeof(float), ctx->stream));
     if (ctx->dim == 3) {
         // diagonal storage: sigma_T (both families), the first source q of every

@@ -6,13 +6,11 @@
 //   sigma_t, sigma_s, q      [J][NXP]
 //   phi    (per sample)      [S][MOM][J][NXP]   current iterate, MOM scalar moments
 //   src    (per sample)      [S][MOM][J][NXP]   source moments for the next sweep
-//   part   (per work item)   [items][MOM][J][NXP]  moments of one item's sweep, or
-//          (per sample)      [S][MOM][J][NXP]      moments accumulated by the sweep
+//   part   (per sample)      [S][MOM][J][NXP]   moments the sweep's work items add
 //   ordinates                c, s, w [M_total] (FP32) and c, s, zeta, w (FP64)
 //   residual partials        [S][chunks][2] FP64
 // MOM = 1 for isotropic scattering (phi), 3 for the linear kernel (phi, Jx, Jy).
-// 3D grids use the same arrays with K * J rows ([K][J][NXP] per sample); their
-// sweep accumulates phi of each sample directly into part [S][K][J][NXP].
+// 3D grids keep the arrays their sweep touches in diagonal storage (Skew3 below).
 #pragma once
 
 #include <cuda.h>
@@ -42,7 +40,7 @@ struct SweepArgs {
     float sigma_t_homog;        // used when the grid has one sigma_T
     const float *sigma_t;       // [J][NXP]
     const float *src;           // [S][MOM][J][NXP]; dense mode: [M_total][J][NXP] per ordinate
-    float *part;                // [items][MOM][J][NXP] (dense mode: one moment, phi)
+    float *part;                // [S][MOM][J][NXP] accumulators (dense mode: phi only)
     float *psi;                 // dense mode: psi of every ordinate [M_total][J][NXP]
     uint32_t *psi_split;        // dense mode, tensor cores: psi as BF16 hi / lo parts,
                                 // [M_total][J * NXP / 8][hi 8 | lo 8] (psi unused when set)
@@ -53,18 +51,15 @@ struct SweepArgs {
     const int *active;          // [S] samples still iterating
     long long cells;            // J * NXP
 };
-// The X-Y sweep adds the moments of the dense mode (mom = 0) to part[sample]
-// (vector atomics; the combine reads and clears them) and stores those of the
-// moment modes to part[item].
+// The X-Y sweep adds the moments of every work item to part[sample] (vector
+// reductions; the combine reads and clears them).
 
 struct CombineArgs {
     int S, MOM, chunks;
-    int zero_part;              // 1: one accumulated part array per sample, read and cleared
     long long cells4;           // J * NXP / 4
     long long cells;
     float g;                    // linear-kernel asymmetry (MOM = 3)
-    const float *part;
-    const int *item_begin;      // [S + 1]
+    float *acc;                 // [S][MOM][cells] moments added by the sweep, cleared here
     float *phi;
     float *src;
     const float *sigma_s, *q;

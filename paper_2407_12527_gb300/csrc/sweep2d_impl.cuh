@@ -87,14 +87,13 @@ __device__ __forceinline__ void red8(float *p, const float (&v)[kCols])
                  "f"(v[6]), "f"(v[7])
                  : "memory");
 }
-// the moments of a row: the dense mode (MOM = 0: many items per sample) adds them
-// to the sample's accumulator, the moment modes store them in the item's own
-// partial array (summed in item order by the combine)
+// the moments of a row, added to the sample's accumulator (every work item of the
+// sample adds into the same array; the reductions run in L2, and the combine reads
+// and clears the array)
 template <int MOM>
 __device__ __forceinline__ void put8(float *p, const float (&v)[kCols])
 {
-    if constexpr (MOM == 0) red8(p, v);
-    else stg8(p, v);
+    red8(p, v);
 }
 // psi of 8 cells as BF16 parts in one 32-byte sector, [8 hi | 8 lo] (the byte
 // layout of the FP32 array): hi = v rounded to the nearest BF16 on its bit
@@ -369,9 +368,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
     for (int m = 0; m < NS; ++m)
         srcp[m] = MOM == 0 ? A.src + (long long)o.ord[m] * A.cells
                            : A.src + ((long long)it.sample * MOM + m) * A.cells;
-    // moments: the sample's accumulator (dense mode) or the item's own partial array
-    float *part_i = A.part + (long long)(MOM == 0 ? it.sample : (int)blockIdx.x) *
-                                 n_out(MOM) * A.cells;
+    // moments: the sample's accumulator [n_out][cells]
+    float *part_i = A.part + (long long)it.sample * n_out(MOM) * A.cells;
 
     // The rows of the lane's block for step t + PD are loaded at the start of
     // step t into a ring of PD + 1 register buffers indexed by t (the same index
