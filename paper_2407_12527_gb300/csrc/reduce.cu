@@ -30,11 +30,6 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-__device__ __forceinline__ float4 add4(float4 a, float4 b)
-{
-    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-}
-
 template <int MOM>
 __global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
 {

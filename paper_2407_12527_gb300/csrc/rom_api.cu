@@ -720,7 +720,6 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     ca.MOM = ctx->MOM == 0 ? 1 : ctx->MOM;
     ca.chunks = ctx->chunks;
     ca.cells = padded_cells(ctx);
-    ca.cells4 = ca.cells / 4;
     ca.g = (float)ctx->g;
     ca.acc = (float *)ctx->part.p;
     ca.phi = (float *)ctx->phi.p;

@@ -56,7 +56,6 @@ struct SweepArgs {
 
 struct CombineArgs {
     int S, MOM, chunks;
-    long long cells4;           // J * NXP / 4
     long long cells;
     float g;                    // linear-kernel asymmetry (MOM = 3)
     float *acc;                 // [S][MOM][cells] moments added by the sweep, cleared here
