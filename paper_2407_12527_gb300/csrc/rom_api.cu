@@ -288,7 +288,6 @@ void set_homog(rom_ctx *ctx, bool homog, float sigma_t)
     ctx->sigma_t_homog = sigma_t;
 }
 
-// 1: isotropic moment, 3: linear-kernel moments, 0: dense operator
 // The sweep adds each sample's moments to one accumulator (vector reductions in
 // L2; the combine reads and clears it) rather than storing per-item partials for
 // the combine to sum: per-item partials would be cells x ordinates in 3D and GB
@@ -298,6 +297,7 @@ void set_homog(rom_ctx *ctx, bool homog, float sigma_t)
 // 3D keeps its accumulators (and source, sigma_T) in diagonal storage, not in part
 bool uses_part(const rom_ctx *ctx) { return ctx->dim == 2; }
 
+// 1: isotropic moment, 3: linear-kernel moments, 0: dense operator
 int source_mode(const rom_ctx *ctx)
 {
     if (ctx->opt.dense_source) return 0;
