@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for the Random Ordinate Method (arXiv 2407.12527), X-Y geometry.
+"""FP64 CPU oracle for the Random Ordinate Method (arXiv 2407.12527), X-Y and 3D geometry.
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and
 the CPU-baseline leg of ``bench.py``, never by the CUDA library or its binding.
@@ -6,7 +6,8 @@ It shares no code with them.
 
 This module holds
   * a ctypes wrapper around ``rom_oracle.c`` (sweeps, source iteration, ROM
-    ordinates, kernel matrix), built with gcc by :func:`build`;
+    ordinates, kernel matrix; X-Y and 3D octant sets and sweeps; the linear
+    kernel's three-moment form), built with gcc by :func:`build`;
   * the deterministic X-Y quadratures of Appendix A (2D uniform, eq. uniform2D;
     2D Gaussian of Lewis & Miller) and a product Gauss-Legendre set, written
     with NumPy (``numpy.polynomial.legendre`` supplies the Legendre roots);
