@@ -145,3 +145,17 @@ def test_tc_hg_disc_full_size_sampled(rom):
                          [O.rom_ordinates_xy(seed, k, 4, 8)], kernel="hg", g=0.8,
                          fixed_iters=3)
         assert rel(gpu["phi"][k], ref["phi"][0]) < TOL, k
+
+
+def test_dense_mode_runs_four_rows_per_step(rom):
+    """The 2-row sweep shape exists for the moment modes only: a dense-operator solve
+    asked for 2 rows per step runs 4 and stays in parity."""
+    I, J = 40, 30
+    st, ss, q = W.random_medium(I, J, seed=19, ratio_max=0.8)
+    gpu = gpu_solve(rom, I, J, (0, 1, 0, 1), st, ss, q, 23, [1, 2], [3, 2], fixed_iters=3,
+                    dense_precision=1, rows_per_step=2)
+    assert gpu["stats"]["rows_per_step"] == 4
+    sets = [O.rom_ordinates_xy(23, k, nz, nt) for k, (nz, nt) in enumerate([(1, 3), (2, 2)])]
+    ref = O.solve_xy(I, J, (0, 1, 0, 1), st, ss, q, sets, kernel="hg", g=0.8, fixed_iters=3)
+    for k in range(2):
+        assert rel(gpu["phi"][k], ref["phi"][k]) < TOL, k

@@ -234,3 +234,26 @@ def test_full_size_lognormal_cube_sampled(rom):
         ref = O.solve_xyz(p.I, p.J, p.K, p.bounds, p.sigma_t, p.sigma_s, p.q, [s],
                           fixed_iters=3)
         assert rel(gpu["phi"][k], ref["phi"][0]) < TOL, k
+
+
+@pytest.mark.parametrize("g", [1, 5])
+def test_3d_context_reuse_new_coefficients_and_reseed(rom, g):
+    """A 3D grid of the same shape keeps the work items and the graph but must see
+    the new coefficients (the diagonal copies are refilled at every solve); a second
+    seeded octant set with the same layout must see the new ordinates."""
+    I, J, K, bounds = GRIDS3[g]
+    ctx = rom.RomContext(0)
+    ctx.set_options(fixed_iters=3)
+    nz, nt = [2, 1], [1, 3]
+    for k, seed in enumerate((41, 42)):
+        st, ss, q = W.random_medium3(I, J, K, seed=seed)
+        ctx.set_grid3(I, J, K, bounds, st, ss, q)
+        first = 4 * k
+        ctx.set_ordinates_seed_xyz(17, nz, nt, first_sample=first)
+        ctx.solve()
+        gpu = np.stack([ctx.scalar_flux(s) for s in range(2)])
+        sets = [O.rom_ordinates_xyz(17, first + s, nz[s], nt[s]) for s in range(2)]
+        ref = O.solve_xyz(I, J, K, bounds, st, ss, q, sets, fixed_iters=3)["phi"]
+        for s in range(2):
+            assert rel(gpu[s], ref[s]) < TOL, (k, s)
+    ctx.close()
