@@ -92,6 +92,8 @@ struct rom_ctx {
     int tuned_h = 0;  // rows per step of that choice
     std::vector<SweepItem> items;
     DevBuf items_dev;
+    float *h_stage = nullptr;  // pinned host staging of rom_set_grid (reused; the call syncs)
+    size_t h_stage_cap = 0;
     // 3D: CTA item lists (one octant each) and the tile hand-off buffers
     std::vector<int> cta_begin, cta_list;
     DevBuf cta_begin_dev, cta_list_dev, xface, yface, err3;
@@ -165,6 +167,23 @@ int ensure(rom_ctx *ctx, DevBuf &b, size_t bytes)
         return fail(ctx, ROM_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
     }
     b.cap = bytes;
+    return ROM_OK;
+}
+
+int ensure_host_stage(rom_ctx *ctx, size_t bytes)
+{
+    if (ctx->h_stage_cap >= bytes) return ROM_OK;
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->h_stage_cap = 0;
+    void *p = nullptr;
+    cudaError_t e = cudaMallocHost(&p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ctx, ROM_ERR_OOM, "cudaMallocHost(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->h_stage = (float *)p;
+    ctx->h_stage_cap = bytes;
     return ROM_OK;
 }
 
@@ -933,6 +952,7 @@ void rom_destroy(rom_ctx *ctx)
                       &ctx->acc3, &ctx->ss3, &ctx->q3, &ctx->psi_split,
                       &ctx->a_hi, &ctx->a_lo, &ctx->tc_err};
     for (DevBuf *b : bufs) release(*b);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->kev) cudaEventDestroy(e);
@@ -990,44 +1010,42 @@ int rom_set_grid(rom_ctx *ctx, int dim, const int64_t n[3], const double lo[3], 
     CK(cudaSetDevice(ctx->device));
     const bool prev = ctx->grid_set;
     ctx->grid_set = false;
-    if ((dim == 2 || dim == 3) && n && n[0] >= 1 && n[1] >= 1 && (dim == 2 || n[2] >= 1) &&
-        n[0] <= 4096 && n[1] <= 4096 && (dim == 2 || n[2] <= 4096)) {
-        const size_t nc = (size_t)n[0] * (size_t)n[1] * (size_t)(dim == 3 ? n[2] : 1);
-        for (size_t k = 0; k < nc; ++k) {
-            const double a = sigma_t[k], b = sigma_s[k], c = q[k];
-            if (!(isfinite(a) && isfinite(b) && isfinite(c) && b >= 0.0 && b < a && c >= 0.0))
-                return fail(ctx, ROM_ERR_INVALID_ARG,
-                            "cell %zu: need 0 <= sigma_S < sigma_T and q >= 0 (got %g, %g, %g)", k,
-                            a, b, c);
-        }
-    }
     int rc = set_grid_common(ctx, prev, dim, n, lo, hi);
     if (rc) return rc;
     const int I = ctx->I, NXP = ctx->NXP;
     const long long J = ctx->rows;  // 3D: the K * J rows of [K][J][I]
-    std::vector<float> hs((size_t)J * NXP), hss((size_t)J * NXP), hq((size_t)J * NXP);
+    const size_t plane = (size_t)J * NXP;
+    if ((rc = ensure_host_stage(ctx, 3 * plane * sizeof(float)))) return rc;
+    // one pass: check the hypotheses, convert to FP32, pad the rows, track min/max
+    // sigma_T; the pinned staging buffer makes the three copies plain DMA
+    float *hs = ctx->h_stage, *hss = hs + plane, *hq = hss + plane;
     double mn = sigma_t[0], mx = sigma_t[0];
-    for (long long j = 0; j < J; ++j)
-        for (int i = 0; i < NXP; ++i) {
-            const size_t d = (size_t)j * NXP + i;
-            if (i < I) {
-                const size_t k = (size_t)j * I + i;
-                hs[d] = (float)sigma_t[k];
-                hss[d] = (float)sigma_s[k];
-                hq[d] = (float)q[k];
-                mn = std::min(mn, sigma_t[k]);
-                mx = std::max(mx, sigma_t[k]);
-            } else {
-                hs[d] = 1.f;
-                hss[d] = 0.f;
-                hq[d] = 0.f;
-            }
+    for (long long j = 0; j < J; ++j) {
+        const double *a = sigma_t + j * I, *b = sigma_s + j * I, *c = q + j * I;
+        float *da = hs + j * NXP, *db = hss + j * NXP, *dc = hq + j * NXP;
+        for (int i = 0; i < I; ++i) {
+            const double x = a[i], y = b[i], z = c[i];
+            if (!(isfinite(x) && isfinite(y) && isfinite(z) && y >= 0.0 && y < x && z >= 0.0))
+                return fail(ctx, ROM_ERR_INVALID_ARG,
+                            "cell %lld: need 0 <= sigma_S < sigma_T and q >= 0 (got %g, %g, %g)",
+                            j * I + i, x, y, z);
+            da[i] = (float)x;
+            db[i] = (float)y;
+            dc[i] = (float)z;
+            mn = std::min(mn, x);
+            mx = std::max(mx, x);
         }
+        for (int i = I; i < NXP; ++i) {
+            da[i] = 1.f;
+            db[i] = 0.f;
+            dc[i] = 0.f;
+        }
+    }
     set_homog(ctx, (float)mn == (float)mx, (float)mn);
-    const size_t bytes = hs.size() * sizeof(float);
-    CK(cudaMemcpyAsync(ctx->sigt.p, hs.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->sigs.p, hss.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->q.p, hq.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+    const size_t bytes = plane * sizeof(float);
+    CK(cudaMemcpyAsync(ctx->sigt.p, hs, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->sigs.p, hss, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->q.p, hq, bytes, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->grid_set = true;
     return ROM_OK;
