@@ -513,6 +513,18 @@ def run_ours(args):
                     "sweep_avg_launch_us": 1e3 * sweep_ms / max(sweep_n, 1),
                     "tile_g": s["tile_g"],
                     "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 flop x 2070 MHz"}
+        if "sweep" in kernel_name and sweep_ms > 0:
+            # the same kernel against HBM: per cell and sample the source moments read
+            # and the flux moments written (4 B each), sigma_T, sigma_S, q shared by the
+            # samples, divided over the sample's ordinates
+            mom = 3 if WL.kernel == "linear" else 1
+            m_avg = WL.m_total() / WL.samples
+            bpu = (8.0 * mom + 12.0 / WL.samples) / m_avg
+            gbs = sweep_upd * bpu / (sweep_ms / 1e3) / 1e9
+            roofline["secondary"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+                                     "unit": "GB/s", "frac": gbs / hbm_peak,
+                                     "bytes_per_update": bpu,
+                                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
 
     # end to end through the C ABI with host buffers
     ctx2 = RomContext(local)
