@@ -364,6 +364,7 @@ def run_ours(args):
         ctx.set_grid_device(p.I, p.J, p.bounds, st_d, ss_d, q_d)
     setup(ctx)
     ctx.set_options(tol=TOL, check_every=args.check_every, tile_g=args.tile_g,
+                    rows_per_step=args.rows_per_step,
                     dense_precision=args.dense_precision)
 
     def first_sample(step):
@@ -425,6 +426,7 @@ def run_ours(args):
     # roofline: the same steps with CUDA events around every sweep (and, for the dense
     # operator, every contraction) launch
     ctx.set_options(tol=TOL, time_kernels=1, check_every=8, tile_g=args.tile_g,
+                    rows_per_step=args.rows_per_step,
                     dense_precision=args.dense_precision)
     sweep_ms, sweep_upd, sweep_n, src_ms, src_n = 0.0, 0, 0, 0.0, 0
     src_flop, src_bytes = 0.0, 0.0
@@ -444,6 +446,7 @@ def run_ours(args):
             # algorithmic HBM bytes of a contraction: psi read + sources written, 4 B each
             src_bytes += 8.0 * M * p.I * p.J * float(np.sum(it))
     ctx.set_options(tol=TOL, check_every=args.check_every, tile_g=args.tile_g,
+                    rows_per_step=args.rows_per_step,
                     dense_precision=args.dense_precision)
     peak_tflops = 152 * 128 * 2 * 2070e6 / 1e12
     homog = float(np.min(p.sigma_t)) == float(np.max(p.sigma_t))
@@ -469,6 +472,8 @@ def run_ours(args):
         traffic = traffic_record("sweep2d_point_source_256", "sweep2d_impl.cuh", WL.samples)
     elif WL.name == "lognormal_cube" and s["tile_g"] == 2:
         traffic = traffic_record("sweep3d_lognormal_cube_128", "sweep3d.cu", WL.samples)
+    elif WL.name == "checkerboard" and s["tile_g"] == 4 and s["rows_per_step"] == 2:
+        traffic = traffic_record("sweep2d_checkerboard_448", "sweep2d_impl.cuh", WL.samples)
     if tc and src_ms > 0:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved / hbm_peak,
@@ -529,7 +534,8 @@ def run_ours(args):
     # end to end through the C ABI with host buffers
     ctx2 = RomContext(local)
     setup(ctx2)
-    ctx2.set_options(tol=TOL, tile_g=args.tile_g, dense_precision=args.dense_precision)
+    ctx2.set_options(tol=TOL, tile_g=args.tile_g, rows_per_step=args.rows_per_step,
+                     dense_precision=args.dense_precision)
     st_h, ss_h, q_h = (np.ascontiguousarray(a, dtype=np.float64) for a in
                        (p.sigma_t, p.sigma_s, p.q))
     e2e_upd, e2e_t = 0, 0.0
@@ -772,6 +778,10 @@ def main():
     ap.add_argument("--check-every", type=int, default=0,
                     help="0: device-side source-iteration loop (CUDA graph); k > 0: host loop "
                          "checking every k sweeps (profilers cannot look inside the graph loop)")
+    ap.add_argument("--rows-per-step", type=int, default=0, choices=[0, 2, 4],
+                    help="X-Y sweep rows per wavefront step (0: 4, or measured with --tile-g -1); "
+                         "fixing it (with --tile-g) reproduces the autotuned shape in profiler "
+                         "captures")
     ap.add_argument("--tile-g", type=int, default=-1,
                     help="ordinates per sweep work item (1, 2, 4; 0: size heuristic; "
                          "-1: measured by the library's autotuner)")
