@@ -98,8 +98,8 @@ typedef struct rom_options {
                      /* them (isotropic; linear without flags), else from the dense        */
                      /* M x M operator; 1: always the dense operator                       */
     int dense_precision; /* the dense operator's product: 0 FP32 (CUDA cores); 1 split     */
-                     /* BF16 on the tensor cores (tcgen05: A_hi Psi_hi + A_hi Psi_lo +     */
-                     /* A_lo Psi_hi, FP32 accumulate, v_hi = v rounded to BF16, v_lo =     */
+                     /* BF16 on the tensor cores (tcgen05: (A_hi + A_lo)(Psi_hi + Psi_lo), */
+                     /* all four products, FP32 accumulate, v_hi = v rounded to BF16, v_lo = */
                      /* bf16(v - v_hi); psi kept as BF16 hi/lo, the bytes of FP32; at most */
                      /* 128 ordinates per sample and 2048 samples per context, else        */
                      /* ROM_ERR_UNSUPPORTED)                                               */

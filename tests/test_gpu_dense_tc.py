@@ -1,7 +1,7 @@
 """GPU parity of the tensor-core dense scattering source (dense_precision = 1).
 
 The dense operator's product D = A Psi runs on the tcgen05 tensor cores in
-split BF16 (A_hi Psi_hi + A_hi Psi_lo + A_lo Psi_hi, FP32 accumulation).  The
+split BF16 ((A_hi + A_lo)(Psi_hi + Psi_lo), all four products, FP32 accumulation).  The
 bar is the one of every other GPU parity test: relative l2 difference of each
 sample's scalar flux <= 1e-5 against the FP64 oracle.  The cases cover uneven M
 per sample (sample row offsets that are not multiples of the 128-row operand
