@@ -345,6 +345,20 @@ def test_quadrature_moments(maker):
     np.testing.assert_allclose(o.c ** 2 + o.s ** 2 + o.zeta ** 2, 1.0, rtol=1e-14)
 
 
+def test_product_gl_set_exact_second_moments():
+    """The 4 polar x 8 azimuthal product set (the 32 x 32 DOM workload): the 4
+    positive roots of L_8 integrate even polynomials in zeta of degree <= 14
+    exactly, and 8 equally spaced azimuths (2j - 1) pi / 8 integrate cos^2, sin^2
+    exactly, so zeta^2, c^2 = (1 - zeta^2) cos^2 theta and s^2 average to 1/3,
+    and zeta^4 to 1/5."""
+    o = O.quad_product_gl_xy(4, 8)
+    assert o.M == 32
+    for f in (o.zeta ** 2, o.c ** 2, o.s ** 2):
+        assert abs(np.sum(o.w * f) - 1.0 / 3.0) < 1e-14
+    assert abs(np.sum(o.w * o.zeta ** 4) - 0.2) < 1e-14
+    assert abs(np.sum(o.w * o.c ** 2 * o.s ** 2) - 1.0 / 15.0) < 1e-14
+
+
 def test_gauss_set_exact_second_moments():
     """The Appendix A Gaussian set integrates zeta^2, c^2 and s^2 exactly (1/3)."""
     for N in (2, 3, 7, 20):
@@ -601,11 +615,18 @@ def test_linear_moment_form_equals_dense_operator(scheme):
         assert list(a["iters"]) == list(b["iters"])
 
 
-def test_example21_ray_effect_measure_dom():
+@pytest.fixture(scope="module")
+def example21_reference():
+    """Example 2.1 on 100 x 100 against the 80400-ordinate Gaussian set (N = 200),
+    the reference of the Sec. 4.2 experiments."""
+    p = W.example_2_1()
+    return p, _solve(p, O.quad_gauss_xy(200), tol=1e-10)
+
+
+def test_example21_ray_effect_measure_dom(example21_reference):
     """e_inf of DOM with 36 and 144 ordinates against the 80400-ordinate Gaussian
     reference (Sec. 4.2), to the printed 3 digits (tests/golden/example21_ray_effect.txt)."""
-    p = W.example_2_1()
-    ref = _solve(p, O.quad_gauss_xy(200), tol=1e-10)
+    p, ref = example21_reference
     with open(os.path.join(GOLDEN, "example21_ray_effect.txt")) as f:
         rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
     for quad, N, M, want in rows:
@@ -664,13 +685,44 @@ def test_randomized_quadrature_error_order_two_dimensions():
 def test_mc_error_order_in_number_of_samples():
     """Sec. 4.1-4.2 (eq. 1dMCerror): the distance of the average of t ROM samples
     from E[phi] falls as t^(-1/2).  E[phi] is the mean of 2048 samples (M = 4,
-    Example 2.1 on 20 x 20); e_MC(t) is the RMS over disjoint groups of t.  A
-    generator whose samples shared draws would flatten the slope."""
+    Example 2.1 on 20 x 20); e_MC(t) is the RMS over disjoint groups of t of
+    O.mc_error.  A generator whose samples shared draws, or an mc_error that
+    averaged over cells instead of samples, would flatten the slope."""
     p = W.example_2_1(I=20, J=20)
     N = 2048
     sets = [O.rom_ordinates_xy(779, k, 1, 1) for k in range(N)]
     phi = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, sets, tol=1e-12)["phi"]
     E = phi.mean(0)
     ts = [4, 8, 16, 32, 64]
-    em = [np.sqrt(np.mean((phi.reshape(N // t, t, p.J, p.I).mean(1) - E) ** 2)) for t in ts]
+    em = [np.sqrt(np.mean([O.mc_error(phi[g * t:(g + 1) * t], E, t) ** 2
+                           for g in range(N // t)])) for t in ts]
     assert -0.65 < _slope(ts, em) < -0.4
+    # with t = all samples the MC error of the mean against itself vanishes
+    assert O.mc_error(phi, E, N) == pytest.approx(0.0, abs=1e-15)
+
+
+def test_rom_error_and_bias_example21(example21_reference):
+    """Sec. 4.2, Table 2dROM_10240: on Example 2.1 with Delta S = pi/16 (M = 16,
+    2 x 2 cells per quadrant) the printed ROM error is 2.26e-2 and the printed bias
+    6.44e-4 (t = 10240).  With t = 256 seeded samples:
+      - rom_error, the mean over samples of the single-run l2 error, lands within
+        3% of 2.26e-2 (its Monte Carlo spread at t = 256 is ~1.5%);
+      - rom_bias, the l2 error of the sample mean, lies between the printed bias
+        and the bias plus the Monte Carlo error of a mean of t samples, whose
+        variance is the samples' mean squared spread / t (taking it as the mean
+        of per-sample errors would give ~2.3e-2);
+      - the exact decomposition mean_s ||phi_s - ref||^2 = ||mean - ref||^2 +
+        mean_s ||phi_s - mean||^2 holds (a mean over the wrong axis breaks it)."""
+    p, ref = example21_reference
+    t = 256
+    sets = [O.rom_ordinates_xy(W.ordinate_seed(7), k, 2, 2) for k in range(t)]
+    phi = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, sets, tol=1e-10)["phi"]
+    err = O.rom_error(phi, ref)
+    assert abs(err - 2.26e-2) < 0.03 * 2.26e-2, err
+    bias = O.rom_bias(phi, ref)
+    mean = O.rom_average(phi)
+    spread2 = np.mean([O.l2_xy(f, mean) ** 2 for f in phi])
+    assert 6.44e-4 <= bias <= 1.5 * np.sqrt(6.44e-4 ** 2 + spread2 / t), (bias, spread2)
+    lhs = np.mean([O.l2_xy(f, ref) ** 2 for f in phi])
+    assert lhs == pytest.approx(bias ** 2 + spread2, rel=1e-10)
+    np.testing.assert_allclose(mean, phi.sum(0) / t, rtol=1e-14)
