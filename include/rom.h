@@ -50,9 +50,10 @@ extern "C" {
 #define ROM_ERR_CUDA (-2)          /* a CUDA runtime call or kernel failed                    */
 #define ROM_ERR_OOM (-3)           /* device or host allocation failed                         */
 #define ROM_ERR_NOT_CONVERGED (-4) /* some sample reached max_iter above tol                   */
-#define ROM_ERR_DIVERGED (-5)      /* a residual became NaN/Inf                                */
+#define ROM_ERR_DIVERGED (-5)      /* a residual became NaN/Inf, or the change kept growing    */
 #define ROM_ERR_STATE (-6)         /* call made before the data it needs was set               */
 #define ROM_ERR_UNSUPPORTED (-7)   /* combination not built (e.g. an anisotropic kernel in 3D) */
+#define ROM_ERR_TIMEOUT (-8)       /* a bounded wait between the warps of a sweep ran out      */
 
 /* --------------------------------------------------------------- choices */
 #define ROM_SCHEME_DD 0   /* diamond difference (Sec. 2)                      */
@@ -107,6 +108,16 @@ typedef struct rom_options {
                      /* or the measured choice with tile_g = -1 (2 or 4); 2 or 4 forces it  */
                      /* (2 only in the isotropic and linear-kernel moment modes, the dense */
                      /* operator mode runs 4); other values are ROM_ERR_INVALID_ARG        */
+    int diverge_window; /* 16: a sample whose change ||phi^k - phi^{k-1}||_2 grew in this  */
+                     /* many consecutive sweeps (while above tol) stops as diverged         */
+                     /* (ROM_ERR_DIVERGED); 0 turns the test off                            */
+    double wait_timeout_ms; /* 2000: bound of every wait of a sweep on another warp (the   */
+                     /* x-edge ring of the 3D sweep, the test hook below); a wait that runs */
+                     /* out ends the sweep and rom_solve returns ROM_ERR_TIMEOUT            */
+    int test_stall_waits; /* 0; 1 makes every sweep warp (X-Y and 3D) wait on an mbarrier  */
+                     /* that nothing completes: a test of the bounded waits -- with a short */
+                     /* wait_timeout_ms the solve returns ROM_ERR_TIMEOUT, and the context  */
+                     /* stays usable                                                       */
 } rom_options;
 
 /* Statistics of the last rom_solve. */
@@ -127,6 +138,11 @@ typedef struct rom_stats {
     int rows_per_step;       /* X-Y sweep: grid rows a lane advances per wavefront step    */
                              /* (4, or 2 when the tile_g = -1 autotuner finds it faster    */
                              /* in the moment modes); 0 for 3D grids                       */
+    double balance_max;      /* X-Y moment modes: largest relative particle-balance error  */
+                             /* of each sample's last sweep (rom_get_balance); NaN when    */
+                             /* not computed (3D, dense operator mode)                     */
+    double phi_min;          /* smallest cell value of phi over the samples' last iterates */
+                             /* (DD is not positive in 2D: it can be < 0)                  */
 } rom_stats;
 
 /* ------------------------------------------------------------- lifetime */
@@ -250,6 +266,19 @@ int rom_get_scalar_flux_device(rom_ctx *ctx, int sample, double *out);
 /* Sweeps each sample took and its last relative change (host arrays [n_samples]). */
 int rom_get_iterations(rom_ctx *ctx, int32_t *iters, double *residuals);
 
+/* Particle balance of each sample's last sweep (host arrays [n_samples], any may be
+ * NULL).  The cell equations of Sec. 2, multiplied by the cell area and summed over
+ * the cells and, with the weights, over the ordinates, telescope to
+ *   L + sum_cells sigma_T phi^k dA = sum_cells sum_l w_l S_l^{k-1} dA,
+ * L = sum_l w_l (|c_l| dy sum_rows + |s_l| dx sum_cols)(psi_out - psi_in) the net
+ * leakage through the boundary, phi^k the sweep's flux, S^{k-1} its source.
+ * leakage receives L (FP64, accumulated from the FP32 boundary values by the
+ * sweep), balance the relative error |L + absorbed - source| / (|L| + |absorbed| +
+ * |source|) with the two cell sums formed in FP64, phi_min the smallest cell value of
+ * phi^k.  X-Y moment modes (isotropic and linear kernel); leakage and balance are NaN
+ * in 3D and in the dense operator mode.  Requires a solve. */
+int rom_get_balance(rom_ctx *ctx, double *leakage, double *balance, double *phi_min);
+
 /* Sum over this context's samples of phi (FP64 [J][I] or [K][J][I]) and their count, for
  * combining runs over disjoint sample ranges (rom_set_ordinates_seed_offset). */
 int rom_get_partial_sum(rom_ctx *ctx, double *sum_out, int64_t *count_out);
@@ -266,11 +295,11 @@ const char *rom_version(void);
  * One transport sweep per sample that allocates no device memory.  The paper
  * has no counterpart: this is a deployment variant of the library's sweep.
  *
- * Who it is for: callers that must not call cudaMalloc -- code running while
- * a CUDA graph is being captured elsewhere in the process, plug-ins whose host
- * application owns all device memory through its own pool, and latency-bound
- * paths where an allocation (and the synchronisation it can imply) is not
- * allowed.  The context API allocates its buffers with cudaMalloc; this call
+ * Who it is for: callers that must not call cudaMalloc -- plug-ins whose host
+ * application owns all device memory through its own pool and forbids other
+ * allocations, and latency-bound paths where an allocation (and the device
+ * synchronisation it can imply) is not allowed.  The context API allocates its
+ * buffers with cudaMalloc; this call
  * instead keeps its scratch (padded copies of the inputs and the per-sample
  * moment accumulators) in one array of ROM_NOALLOC_SCRATCH_BYTES that the library
  * places in device memory when it is loaded.  Every GPU that loads the
@@ -298,8 +327,10 @@ const char *rom_version(void);
  * routine is called.
  *
  * Behaviour: the first call on a device (with that device current) looks up
- * the device address of the scratch array once and caches it; make that first
- * call before any stream capture.  The call returns after enqueueing the work;
+ * the device address of the scratch array once and caches it for the life of the
+ * process; make that first call before any stream capture.  After
+ * cudaDeviceReset on a device the cached address is stale: do not call this entry
+ * point on that device again in the same process.  The call returns after enqueueing the work;
  * phi is ready when the stream reaches that point.  All calls on a device share
  * the one scratch array, which keeps the last call's contents; no part of it
  * needs to start at zero, because every call writes (or clears) each byte it

@@ -1,11 +1,10 @@
 // noalloc.cu -- rom_sweep_xy_noalloc: one transport sweep that allocates no
 // device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured elsewhere in the process, plug-ins whose host application
-// owns all device memory through its own pool, or real-time code paths where
-// an allocation (and the implicit synchronisation it may bring) is not
-// allowed.  For them this entry point runs the sweep kernel of the library with
+// Some callers cannot call cudaMalloc: plug-ins whose host application owns
+// all device memory through its own pool and forbids other allocations, or
+// real-time code paths where an allocation (and the implicit device
+// synchronisation it may bring) is not allowed.  For them this entry point runs the sweep kernel of the library with
 // its scratch memory -- padded copies of the inputs and the per-sample moment
 // accumulators -- placed in one fixed-size array in the library's own
 // device memory instead of in buffers it would allocate.
@@ -15,8 +14,13 @@
 // or not the entry point is called.  Host code must not use the name of the
 // array as a pointer (on the host it is only a stand-in symbol); the device
 // address is obtained once per device with cudaGetSymbolAddress, on the first
-// call made with that device current, and cached.  Because of that one-time
-// set-up, make the first call on each device before any stream capture.
+// call made with that device current, and cached for the life of the process.
+// Because of that one-time set-up, make the first call on each device before
+// any stream capture; after cudaDeviceReset the cached address is stale, so the
+// entry point must not be used again on a reset device.  The small tables are
+// staged in a static host table and copied with cudaMemcpyAsync from pageable
+// memory, which returns only once the source bytes have been taken, so the next
+// call may overwrite the table.
 //
 // All calls on a device share the array and it keeps the contents of the last
 // call.  Nothing in it has to start at zero: every call overwrites (or clears)

@@ -9,8 +9,18 @@
 //           (eq. equ_random with eq. anisotropic kernel, mirror-averaged in
 //           zeta, where sum_l' w_l' (1 + g u_l'.u_l) psi_l' = phi + g (c Jx + s Jy)),
 //           and per-block FP64 partial sums of |phi^k - phi^{k-1}|^2 and |phi^k|^2
-//           (each thread first sums the squares of its few cells in FP32; the
-//           FP64 units of GB300 are few, so FP64 is used from the warp sums on).
+//           (and, in the X-Y moment modes, of sigma_T phi^k and of the previous
+//           iterate's source moments, for the particle balance), and min phi.
+//           Summation precision: each thread sums its few cells (8 to 32) in
+//           FP32, the 32 lanes of a warp add by an FP32 tree (5 levels), and from
+//           the warp sums on everything is FP64 (across warps, blocks and in the
+//           finalize).  A term passes through at most ~37 FP32 additions, so the
+//           relative error of each block partial is below ~37 * 2^-24 = 2.2e-6
+//           in the worst case (random rounding: ~sqrt(37) * 2^-24 = 3.6e-7); the
+//           relative residual sqrt(d2 / n2) then carries about half of that,
+//           well below the tolerances of 1e-6 and above that FP32 sweeps reach.
+//           The FP64 units of GB300 are few: a per-thread FP64 sum (or an FP64
+//           warp tree) in every combine block costs more than the FP32 work.
 // finalize: relative l2 change per sample (Sec. 3.2 source iteration stopping
 //           rule of this library), sweep counters, the active flags, and the
 //           number of samples still iterating (optionally the condition of the
@@ -23,11 +33,36 @@
 namespace romk {
 namespace {
 
-__device__ __forceinline__ double warp_sum(double v)
+// The block's partials: six FP32 per-thread sums (squared change, squared
+// norm, sigma_T phi, three source moments) and a min, summed by an FP32 warp
+// tree, then in FP64 across the warps; written to out[0 .. kNP-1].  Every
+// thread of the block calls it.
+__device__ __forceinline__ void block_partials(float (&v)[6], float mn, double *out)
 {
+    __shared__ double red[6][32];
+    __shared__ float redm[32];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) red[k][w] = (double)v[k];
+        redm[w] = mn;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double acc = 0.0;
+        for (int k = 0; k < nw; ++k) acc += red[threadIdx.x][k];
+        out[threadIdx.x] = acc;
+    } else if (threadIdx.x == 6) {
+        float m = redm[0];
+        for (int k = 1; k < nw; ++k) m = fminf(m, redm[k]);
+        out[6] = (double)m;
+    }
 }
 
 template <int MOM>
@@ -38,14 +73,36 @@ __global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
     const long long cells = A.cells;  // a multiple of 8: every thread owns one 32-byte sector
     float *phi = A.phi + (long long)s * MOM * cells;
     float *src = A.src + (long long)s * MOM * cells;
-    float d2f = 0.f, n2f = 0.f;
+    float d2f = 0.f, n2f = 0.f, mn = INFINITY, a1f = 0.f, b0f = 0.f, b1f = 0.f, b2f = 0.f;
     for (long long v = 8 * ((long long)blockIdx.x * blockDim.x + threadIdx.x); v < cells;
          v += 8LL * gridDim.x * blockDim.x) {
         float acc[MOM][8];
-        float old[8], ss[8], qq[8], out[8];
+        float old[8], ss[8], qq[8], out[8], st[8];
         ld8_volatile(phi + v, old);
         ldg8(A.sigma_s + v, ss);
         ldg8(A.q + v, qq);
+        if (A.balance) {
+            // the source moments of the previous iterate (the sweep's input) and
+            // sigma_T phi of the new one, for the particle balance; padding
+            // columns hold phi = 0 and sigma_S = q = 0
+            if (A.sigma_t) ldg8(A.sigma_t + v, st);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) b0f += fmaf(ss[e], old[e], qq[e]);
+            if (MOM == 3) {
+                float o1[8], o2[8];
+                ld8_volatile(phi + cells + v, o1);
+                ld8_volatile(phi + 2 * cells + v, o2);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    b1f = fmaf(A.g * ss[e], o1[e], b1f);
+                    b2f = fmaf(A.g * ss[e], o2[e], b2f);
+                }
+            }
+            // the accumulated moments are read below; sigma_T phi is added there
+            if (!A.sigma_t)
+#pragma unroll
+                for (int e = 0; e < 8; ++e) st[e] = A.sigma_t_homog;
+        }
         {  // the sample's accumulated moments, cleared for the next sweep
             float zero[8];
 #pragma unroll
@@ -63,6 +120,9 @@ __global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
             const float dd = acc[0][e] - old[e];
             d2f = fmaf(dd, dd, d2f);
             n2f = fmaf(acc[0][e], acc[0][e], n2f);
+            if (A.balance) a1f = fmaf(st[e], acc[0][e], a1f);  // sigma_T phi
+            // padding columns (x >= I) hold phi = 0 and would hide a negative min
+            if ((v % A.NXP) + e < A.I) mn = fminf(mn, acc[0][e]);
         }
 #pragma unroll
         for (int m = 0; m < MOM; ++m) stg8(phi + m * cells + v, acc[m]);
@@ -78,26 +138,8 @@ __global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
             }
         }
     }
-    __shared__ double red[2][32];
-    double d2 = warp_sum((double)d2f);
-    double n2 = warp_sum((double)n2f);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[0][w] = d2;
-        red[1][w] = n2;
-    }
-    __syncthreads();
-    if (w == 0) {
-        const int nw = blockDim.x >> 5;
-        d2 = lane < nw ? red[0][lane] : 0.0;
-        n2 = lane < nw ? red[1][lane] : 0.0;
-        d2 = warp_sum(d2);
-        n2 = warp_sum(n2);
-        if (lane == 0) {
-            A.partials[((long long)s * A.chunks + blockIdx.x) * 2 + 0] = d2;
-            A.partials[((long long)s * A.chunks + blockIdx.x) * 2 + 1] = n2;
-        }
-    }
+    float v6[6] = {d2f, n2f, a1f, b0f, b1f, b2f};
+    block_partials(v6, mn, A.partials + ((long long)s * A.chunks + blockIdx.x) * kNP);
 }
 
 // 3D: phi of each sample from its two diagonal-storage accumulators (read and
@@ -117,7 +159,7 @@ __global__ void __launch_bounds__(256) combine3_kernel(const Combine3Args A)
     float *src0 = A.src + (long long)s * g.cells;
     float *src1 = A.src + ((long long)A.S + s) * g.cells;
     float *phi = A.phi + (long long)s * g.cells;
-    float d2f = 0.f, n2f = 0.f;
+    float d2f = 0.f, n2f = 0.f, mn = INFINITY;
     for (int sec = blockIdx.x * blockDim.x + threadIdx.x; sec < n_sec;
          sec += gridDim.x * blockDim.x) {
         // sec = ((diag * L + strip) * 4 + hh) * NBg + jb
@@ -142,6 +184,7 @@ __global__ void __launch_bounds__(256) combine3_kernel(const Combine3Args A)
             const float dd = now[e] - old[e];
             d2f = fmaf(dd, dd, d2f);
             n2f = fmaf(now[e], now[e], n2f);
+            if (strip * 8 + e < A.I) mn = fminf(mn, now[e]);
             out[e] = fmaf(ss[e], now[e], qq[e]);
         }
         stg8(acc0 + i0, zero);
@@ -150,26 +193,8 @@ __global__ void __launch_bounds__(256) combine3_kernel(const Combine3Args A)
         stg8(src0 + i0, out);
         stg8(src1 + i1, out);
     }
-    __shared__ double red[2][32];
-    double d2 = warp_sum((double)d2f);
-    double n2 = warp_sum((double)n2f);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[0][w] = d2;
-        red[1][w] = n2;
-    }
-    __syncthreads();
-    if (w == 0) {
-        const int nw = blockDim.x >> 5;
-        d2 = lane < nw ? red[0][lane] : 0.0;
-        n2 = lane < nw ? red[1][lane] : 0.0;
-        d2 = warp_sum(d2);
-        n2 = warp_sum(n2);
-        if (lane == 0) {
-            A.partials[((long long)s * A.chunks + blockIdx.x) * 2 + 0] = d2;
-            A.partials[((long long)s * A.chunks + blockIdx.x) * 2 + 1] = n2;
-        }
-    }
+    float v6[6] = {d2f, n2f, 0.f, 0.f, 0.f, 0.f};
+    block_partials(v6, mn, A.partials + ((long long)s * A.chunks + blockIdx.x) * kNP);
 }
 
 // 3D average / extraction from family-0 diagonal storage [S][sk.cells] into [K][J][I]
@@ -226,20 +251,47 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalizeArgs A)
     int cnt = 0;
     for (int s = threadIdx.x; s < A.S; s += blockDim.x) {
         if (!A.active[s]) continue;
-        double d2 = 0.0, n2 = 0.0;
+        double d2 = 0.0, n2 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, mn = INFINITY;
         for (int c = 0; c < A.chunks; ++c) {
-            d2 += A.partials[((long long)s * A.chunks + c) * 2 + 0];
-            n2 += A.partials[((long long)s * A.chunks + c) * 2 + 1];
+            const double *p = A.partials + ((long long)s * A.chunks + c) * kNP;
+            d2 += p[0];
+            n2 += p[1];
+            a1 += p[2];
+            b0 += p[3];
+            b1 += p[4];
+            b2 += p[5];
+            mn = fmin(mn, p[6]);
         }
         const double r = n2 > 0.0 ? sqrt(d2 / n2) : (d2 == 0.0 ? 0.0 : (double)INFINITY);
         const int it = A.iters[s] + 1;
         A.iters[s] = it;
         A.resid[s] = r;
         const bool bad = !isfinite(r);
+        // divergence: the change ||phi^k - phi^{k-1}|| itself grows sweep after
+        // sweep (for a contracting iteration it shrinks by the spectral radius)
+        const double dn = sqrt(d2);
+        const int gr = (dn > A.dprev[s] && !(r < A.tol)) ? A.grow[s] + 1 : 0;
+        A.grow[s] = gr;
+        A.dprev[s] = dn;
+        const bool growing = A.diverge_window > 0 && gr >= A.diverge_window;
         if (bad) A.flags[s] |= 1;
+        if (growing) A.flags[s] |= 2;
+        A.phimin_out[s] = mn;
+        if (A.balance) {
+            // leakage + sum sigma_T phi^k dA = sum_l w_l sum S_l^{k-1} dA, exact for
+            // the cell equations of the sweep up to its rounding
+            const double lk = A.leak[s];
+            A.leak[s] = 0.0;
+            const double *os = A.ordsum + 3LL * s;
+            const double rhs = A.dA * (os[0] * b0 + os[1] * b1 + os[2] * b2);
+            const double rem = A.dA * a1;
+            const double den = fabs(lk) + fabs(rem) + fabs(rhs);
+            A.bal_out[s] = den > 0.0 ? fabs(lk + rem - rhs) / den : 0.0;
+            A.leak_out[s] = lk;
+        }
         bool stop;
         if (A.fixed_iters > 0) stop = it >= A.fixed_iters;
-        else stop = (r < A.tol) || it >= A.max_iter || bad;
+        else stop = (r < A.tol) || it >= A.max_iter || bad || growing;
         if (stop) A.active[s] = 0;
         else ++cnt;
     }
@@ -254,6 +306,35 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalizeArgs A)
         *A.n_active = tot;
         if (A.use_cond) cudaGraphSetConditional(A.cond, tot > 0 ? 1u : 0u);
     }
+}
+
+__global__ void init_checks_kernel(int S, double *dprev, int *grow, double *leak, double *bal,
+                                   double *leak_out, double *phimin)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    dprev[s] = (double)INFINITY;
+    grow[s] = 0;
+    leak[s] = 0.0;
+    bal[s] = (double)NAN;
+    leak_out[s] = (double)NAN;
+    phimin[s] = (double)NAN;
+}
+
+__global__ void ordsum_kernel(const double *c, const double *s, const double *w,
+                              const long long *ord_off, const int *M, int S, double *out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= S) return;
+    double sw = 0.0, swc = 0.0, sws = 0.0;
+    for (long long o = ord_off[k]; o < ord_off[k] + M[k]; ++o) {
+        sw += w[o];
+        swc += w[o] * c[o];
+        sws += w[o] * s[o];
+    }
+    out[3 * k] = sw;
+    out[3 * k + 1] = swc;
+    out[3 * k + 2] = sws;
 }
 
 __global__ void init_state_kernel(int S, int MOM, long long cells, const float *q, float *phi,
@@ -427,6 +508,22 @@ cudaError_t launch_pad_grid(const float *st_in, const float *ss_in, const float 
 {
     pad_grid_kernel<<<blocks_for((long long)J * NXP, 256), 256, 0, st>>>(
         st_in, ss_in, q_in, I, J, NXP, st_out, ss_out, q_out, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ordsum(const double *c, const double *s, const double *w,
+                          const long long *ord_off, const int *M, int S, double *out,
+                          cudaStream_t st)
+{
+    ordsum_kernel<<<(S + 127) / 128, 128, 0, st>>>(c, s, w, ord_off, M, S, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_checks(int S, double *dprev, int *grow, double *leak, double *bal,
+                               double *leak_out, double *phimin, cudaStream_t st)
+{
+    init_checks_kernel<<<(S + 255) / 256, 256, 0, st>>>(S, dprev, grow, leak, bal, leak_out,
+                                                        phimin);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,8 @@
 namespace romk {
 int host_quadrature(int kind, int n1, int n2, std::vector<double> &c, std::vector<double> &s,
                     std::vector<double> &z, std::vector<double> &w);
-}
+
+}  // namespace romk
 
 using romk::SweepItem;
 
@@ -90,6 +91,12 @@ struct rom_ctx {
     int H_used = 4;   // X-Y sweep: rows a lane advances per wavefront step
     int tuned_g = 0;  // measured choice (tile_g = -1), valid while the layout is unchanged
     int tuned_h = 0;  // rows per step of that choice
+    // per-sample tables of the balance: first ordinate and count, weight sums
+    DevBuf otab, ordsum;
+    // per-sample divergence and balance state: dprev, grow, leak (added by the
+    // sweep), bal / leak_out / phimin (last sweep); the X-Y sweep's wait flag
+    DevBuf dprev, grow, leak, bal, leak_out, phimin, sweep_err;
+    std::vector<double> h_bal, h_leak, h_phimin;
     std::vector<SweepItem> items;
     DevBuf items_dev;
     float *h_stage = nullptr;  // pinned host staging of rom_set_grid (reused; the call syncs)
@@ -313,8 +320,8 @@ void set_homog(rom_ctx *ctx, bool homog, float sigma_t)
 // in the dense mode, and in the X-Y moment modes the accumulator measured 19%
 // faster per source iteration (the sweep writes less, the combine reads one
 // array).  The price is the order of the additions, which follows the timing.
-// 3D keeps its accumulators (and source, sigma_T) in diagonal storage, not in part
-bool uses_part(const rom_ctx *ctx) { return ctx->dim == 2; }
+// 3D keeps its accumulators (and source, sigma_T) in diagonal storage, not in part;
+// the X-Y moment modes keep theirs in part, in sheared storage.
 
 // 1: isotropic moment, 3: linear-kernel moments, 0: dense operator
 int source_mode(const rom_ctx *ctx)
@@ -334,6 +341,10 @@ int choose_rows(const rom_ctx *ctx)
     if (ctx->opt.tile_g == -1 && ctx->tuned_h > 0) return ctx->tuned_h;
     return 4;
 }
+
+// X-Y moment modes: the particle balance is formed from the sweep's leakage and
+// the combine's partial sums
+bool has_balance(const rom_ctx *ctx) { return ctx->dim == 2 && source_mode(ctx) != 0; }
 
 int choose_g(const rom_ctx *ctx)
 {
@@ -480,6 +491,14 @@ int build_items(rom_ctx *ctx)
     if (!ctx->items.empty())
         CK(cudaMemcpyAsync(ctx->items_dev.p, ctx->items.data(), ctx->items.size() * sizeof(SweepItem),
                            cudaMemcpyHostToDevice, ctx->stream));
+    // first ordinate and count per sample ([S] long long, [S] int), for the
+    // per-sample weight sums of the balance
+    const size_t tb = (size_t)ctx->S * (sizeof(long long) + sizeof(int));
+    if ((rc = ensure(ctx, ctx->otab, tb))) return rc;
+    std::vector<unsigned char> h(tb);
+    memcpy(h.data(), ctx->off.data(), ctx->S * sizeof(long long));
+    memcpy(h.data() + ctx->S * sizeof(long long), ctx->M.data(), ctx->S * sizeof(int));
+    CK(cudaMemcpyAsync(ctx->otab.p, h.data(), tb, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));  // host vectors may change before the next use
     ctx->items_dirty = false;
     return ROM_OK;
@@ -541,6 +560,12 @@ romk::SweepArgs sweep_args(const rom_ctx *ctx)
     a.inflow_stride = ctx->inflow_stride;
     a.active = (const int *)ctx->active.p;
     a.cells = (long long)ctx->J * ctx->NXP;
+    a.leak = has_balance(ctx) ? (double *)ctx->leak.p : nullptr;
+    a.dx = (float)((ctx->hi[0] - ctx->lo[0]) / ctx->I);
+    a.dy = (float)((ctx->hi[1] - ctx->lo[1]) / ctx->J);
+    a.err = (int *)ctx->sweep_err.p;
+    a.wait_ns = (unsigned long long)(ctx->opt.wait_timeout_ms * 1e6);
+    a.stall = ctx->opt.test_stall_waits;
     if (ctx->MOM == 0) {
         a.src = (const float *)ctx->src_ord.p;
         if (ctx->opt.dense_precision == 1) {
@@ -583,6 +608,8 @@ romk::Sweep3Args sweep3_args(const rom_ctx *ctx)
     a.xface = (float *)ctx->xface.p;
     a.yface = (float *)ctx->yface.p;
     a.err = (int *)ctx->err3.p;
+    a.wait_ns = (unsigned long long)(ctx->opt.wait_timeout_ms * 1e6);
+    a.stall = ctx->opt.test_stall_waits;
     return a;
 }
 
@@ -736,6 +763,8 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     if (k1) CK(cudaEventRecord(k1, st));
     romk::CombineArgs ca{};
     ca.S = ctx->S;
+    ca.I = ctx->I;
+    ca.NXP = ctx->NXP;
     ca.MOM = ctx->MOM == 0 ? 1 : ctx->MOM;
     ca.chunks = ctx->chunks;
     ca.cells = padded_cells(ctx);
@@ -747,6 +776,9 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     ca.q = (const float *)ctx->q.p;
     ca.active = (const int *)ctx->active.p;
     ca.partials = (double *)ctx->partials.p;
+    ca.balance = has_balance(ctx) ? 1 : 0;
+    ca.sigma_t = ctx->homog ? nullptr : (const float *)ctx->sigt.p;
+    ca.sigma_t_homog = ctx->sigma_t_homog;
     if (ctx->dim == 3) {
         romk::Combine3Args c3{};
         c3.S = ctx->S;
@@ -759,6 +791,7 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
         c3.q = (const float *)ctx->q3.p;
         c3.active = (const int *)ctx->active.p;
         c3.partials = (double *)ctx->partials.p;
+        c3.I = ctx->I;
         CK(romk::launch_combine3(c3, st));
     } else {
         CK(romk::launch_combine(ca, st));
@@ -794,12 +827,24 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     fa.iters = (int *)ctx->iters.p;
     fa.flags = (int *)ctx->flags.p;
     fa.resid = (double *)ctx->resid.p;
+    fa.diverge_window = ctx->opt.diverge_window;
+    fa.dprev = (double *)ctx->dprev.p;
+    fa.grow = (int *)ctx->grow.p;
+    fa.balance = has_balance(ctx) ? 1 : 0;
+    fa.leak = (double *)ctx->leak.p;
+    fa.dA = (ctx->hi[0] - ctx->lo[0]) / ctx->I * (ctx->hi[1] - ctx->lo[1]) / ctx->J;
+    fa.ordsum = (const double *)ctx->ordsum.p;
+    fa.bal_out = (double *)ctx->bal.p;
+    fa.leak_out = (double *)ctx->leak_out.p;
+    fa.phimin_out = (double *)ctx->phimin.p;
     fa.n_active = (int *)ctx->n_active.p;
     fa.use_cond = use_cond ? 1 : 0;
     fa.cond = h;
     CK(romk::launch_finalize(fa, st));
     return ROM_OK;
 }
+
+int ensure_state(rom_ctx *ctx);
 
 // tile_g = -1: time the sweep kernel of every candidate work-item size G and
 // rows per wavefront step H (2 only in the moment modes) on the current problem
@@ -817,8 +862,7 @@ int autotune_g(rom_ctx *ctx)
         if (G > cap || (want_h != 0 && H != want_h)) continue;
         ctx->opt.tile_g = G;
         if ((rc = build_items(ctx))) return rc;
-        if ((rc = ensure(ctx, ctx->part, (size_t)ctx->S * MOMk * cells * sizeof(float))))
-            return rc;
+        if ((rc = ensure_state(ctx))) return rc;  // phi, sources, accumulators
         CK(romk::launch_init_state(ctx->S, MOMk, cells, (const float *)ctx->q.p,
                                    (float *)ctx->phi.p, (float *)ctx->src.p, (int *)ctx->active.p,
                                    (int *)ctx->iters.p, (int *)ctx->flags.p,
@@ -848,6 +892,91 @@ int autotune_g(rom_ctx *ctx)
     ctx->tuned_g = best;
     ctx->tuned_h = best_h;
     ctx->items_dirty = true;
+    return ROM_OK;
+}
+
+// Per-sample state arrays of the current layout -- phi, the source moments and
+// the sweep's accumulators in row-major (dense operator mode), sheared (X-Y
+// moment modes) or diagonal (3D) storage -- and the sheared coefficient copies.
+int ensure_state(rom_ctx *ctx)
+{
+    int rc;
+    const int MOM = ctx->MOM == 0 ? 1 : ctx->MOM;
+    const size_t S = ctx->S;
+    if (ctx->dim == 3) {
+        const romk::Skew3 sk = romk::make_skew3(ctx->J, ctx->K, ctx->NXP);
+        if (sk.cells >= (1LL << 31))
+            return fail(ctx, ROM_ERR_UNSUPPORTED, "3D grid too large for one sample's arrays");
+        const size_t b = (size_t)sk.cells * sizeof(float);
+        if ((rc = ensure(ctx, ctx->sig3, 2 * b)) || (rc = ensure(ctx, ctx->src3, 2 * S * b)) ||
+            (rc = ensure(ctx, ctx->acc3, 2 * S * b)) || (rc = ensure(ctx, ctx->ss3, b)) ||
+            (rc = ensure(ctx, ctx->q3, b)) || (rc = ensure(ctx, ctx->phi, S * b)))
+            return rc;
+        return ROM_OK;
+    }
+    const size_t b = (size_t)padded_cells(ctx) * sizeof(float);
+    if ((rc = ensure(ctx, ctx->phi, S * MOM * b)) || (rc = ensure(ctx, ctx->src, S * MOM * b)) ||
+        (rc = ensure(ctx, ctx->part, S * MOM * b)))
+        return rc;
+    return ROM_OK;
+}
+
+// Device state of a new solve, on the context stream: phi^0 = 0, the first
+// source q (psi^0 = 0), cleared accumulators and error words, every sample
+// active, the coefficient copies of the layout, the divergence and balance
+// state, and the per-sample weight sums of the balance.
+int init_state(rom_ctx *ctx)
+{
+    const int MOM = ctx->MOM == 0 ? 1 : ctx->MOM;
+    const long long cells = padded_cells(ctx);
+    cudaStream_t st = ctx->stream;
+    if (ctx->MOM == 0 && ctx->opt.dense_precision == 1)
+        CK(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(ctx->sweep_err.p, 0, sizeof(int), st));
+    if (ctx->dim == 3) {
+        // diagonal storage: sigma_T (both families), the first source q of every
+        // sample, sigma_S and q for the combine (family 0), cleared accumulators, phi = 0
+        const romk::Skew3 sk = romk::make_skew3(ctx->J, ctx->K, ctx->NXP);
+        CK(cudaMemsetAsync(ctx->err3.p, 0, sizeof(int), st));
+        CK(cudaMemsetAsync(ctx->acc3.p, 0, 2 * (size_t)ctx->S * sk.cells * sizeof(float), st));
+        CK(romk::launch_skew3_scatter((const float *)ctx->sigt.p, sk, ctx->NXP, 2, 1,
+                                      (float *)ctx->sig3.p, st));
+        CK(romk::launch_skew3_scatter((const float *)ctx->q.p, sk, ctx->NXP, 2, ctx->S,
+                                      (float *)ctx->src3.p, st));
+        CK(romk::launch_skew3_scatter((const float *)ctx->sigs.p, sk, ctx->NXP, 1, 1,
+                                      (float *)ctx->ss3.p, st));
+        CK(romk::launch_skew3_scatter((const float *)ctx->q.p, sk, ctx->NXP, 1, 1,
+                                      (float *)ctx->q3.p, st));
+        ctx->launches += 4;
+        CK(romk::launch_init_state(ctx->S, 1, sk.cells, nullptr, (float *)ctx->phi.p, nullptr,
+                                   (int *)ctx->active.p, (int *)ctx->iters.p, (int *)ctx->flags.p,
+                                   (double *)ctx->resid.p, st));
+    } else {
+        // the sweep accumulates into part; the combine clears it
+        CK(cudaMemsetAsync(ctx->part.p, 0, (size_t)ctx->S * MOM * cells * sizeof(float), st));
+        CK(romk::launch_init_state(ctx->S, MOM, cells, (const float *)ctx->q.p,
+                                   (float *)ctx->phi.p, (float *)ctx->src.p, (int *)ctx->active.p,
+                                   (int *)ctx->iters.p, (int *)ctx->flags.p,
+                                   (double *)ctx->resid.p, st));
+    }
+    ++ctx->launches;
+    if (ctx->MOM == 0) {  // psi^0 = 0: every ordinate's first source is q
+        CK(romk::launch_dense_init((const float *)ctx->q.p, cells, ctx->Mtot,
+                                   (float *)ctx->src_ord.p, st));
+        ++ctx->launches;
+    }
+    CK(romk::launch_init_checks(ctx->S, (double *)ctx->dprev.p, (int *)ctx->grow.p,
+                                (double *)ctx->leak.p, (double *)ctx->bal.p,
+                                (double *)ctx->leak_out.p, (double *)ctx->phimin.p, st));
+    ++ctx->launches;
+    if (has_balance(ctx)) {
+        const unsigned char *ot = (const unsigned char *)ctx->otab.p;
+        CK(romk::launch_ordsum((const double *)ctx->c64.p, (const double *)ctx->s64.p,
+                               (const double *)ctx->w64.p, (const long long *)ot,
+                               (const int *)(ot + ctx->S * sizeof(long long)), ctx->S,
+                               (double *)ctx->ordsum.p, st));
+        ++ctx->launches;
+    }
     return ROM_OK;
 }
 
@@ -905,6 +1034,9 @@ void rom_default_options(rom_options *opt)
     opt->dense_source = 0;
     opt->dense_precision = 0;
     opt->rows_per_step = 0;
+    opt->diverge_window = 16;
+    opt->wait_timeout_ms = 2000.0;
+    opt->test_stall_waits = 0;
 }
 
 int rom_create(rom_ctx **out, int cuda_device)
@@ -950,7 +1082,9 @@ void rom_destroy(rom_ctx *ctx)
                       &ctx->dtab, &ctx->z32, &ctx->cta_begin_dev, &ctx->cta_list_dev,
                       &ctx->xface, &ctx->yface, &ctx->err3, &ctx->sig3, &ctx->src3,
                       &ctx->acc3, &ctx->ss3, &ctx->q3, &ctx->psi_split,
-                      &ctx->a_hi, &ctx->a_lo, &ctx->tc_err};
+                      &ctx->a_hi, &ctx->a_lo, &ctx->tc_err, &ctx->otab, &ctx->ordsum,
+                      &ctx->dprev, &ctx->grow,
+                      &ctx->leak, &ctx->bal, &ctx->leak_out, &ctx->phimin, &ctx->sweep_err};
     for (DevBuf *b : bufs) release(*b);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -991,6 +1125,11 @@ int rom_set_options(rom_ctx *ctx, const rom_options *opt)
         return fail(ctx, ROM_ERR_INVALID_ARG, "dense_precision must be 0 or 1");
     if (opt->rows_per_step != 0 && opt->rows_per_step != 2 && opt->rows_per_step != 4)
         return fail(ctx, ROM_ERR_INVALID_ARG, "rows_per_step must be 0, 2 or 4");
+    if (opt->diverge_window < 0) return fail(ctx, ROM_ERR_INVALID_ARG, "diverge_window < 0");
+    if (!(opt->wait_timeout_ms > 0.0) || !(opt->wait_timeout_ms <= 6e5))
+        return fail(ctx, ROM_ERR_INVALID_ARG, "wait_timeout_ms must be in (0, 600000]");
+    if (opt->test_stall_waits != 0 && opt->test_stall_waits != 1)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "test_stall_waits must be 0 or 1");
     if (opt->tile_g != ctx->opt.tile_g || opt->dense_source != ctx->opt.dense_source ||
         opt->dense_precision != ctx->opt.dense_precision ||
         opt->rows_per_step != ctx->opt.rows_per_step) {
@@ -1401,6 +1540,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     int rc;
     const long long cells = padded_cells(ctx);
     const int mode = source_mode(ctx);
+    const int MOM = mode == 0 ? 1 : mode;  // moments kept per sample
     if (ctx->dim == 3 && mode != 1)
         return fail(ctx, ROM_ERR_UNSUPPORTED,
                     "3D grids support the isotropic kernel with angular moments only");
@@ -1420,41 +1560,31 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     // residual chunks: combine blocks of 256 threads per sample, each thread
     // taking one or more 8-cell sectors; about 16 blocks per SM in all, so that
     // large grids stream many sectors per thread instead of paying the block's
-    // FP64 reduction per sector, and the finalize adds few partials per sample
+    // reduction per sector, and the finalize adds few partials per sample
     const long long max_chunks = std::max<long long>(1, (cells / 8 + 255) / 256);
     const long long want = std::max<long long>(1, (16LL * ctx->sm_count + ctx->S - 1) / ctx->S);
     const int chunks = (int)std::min(max_chunks, want);
     if (chunks != ctx->chunks) invalidate_graph(ctx);
     ctx->chunks = chunks;
-    const int MOM = ctx->MOM == 0 ? 1 : ctx->MOM;  // moments kept per sample
-    // 3D keeps phi in family-0 diagonal storage and its source in src3 only
-    const size_t state = ctx->dim == 3 ? (size_t)ctx->S * romk::make_skew3(ctx->J, ctx->K,
-                                                                            ctx->NXP).cells *
-                                             sizeof(float)
-                                       : (size_t)ctx->S * MOM * cells * sizeof(float);
-    const size_t src_bytes = ctx->dim == 3 ? 0 : state;
     const size_t nI = (size_t)n_cells(ctx);
-    // part: the moments of each sample, accumulated by the sweep (X-Y)
-    const size_t part_units = uses_part(ctx) ? (size_t)ctx->S : 0;
-    if (ctx->dim == 3) {
-        const romk::Skew3 sk = romk::make_skew3(ctx->J, ctx->K, ctx->NXP);
-        if (sk.cells >= (1LL << 31))
-            return fail(ctx, ROM_ERR_UNSUPPORTED, "3D grid too large for one sample's arrays");
-        const size_t b = (size_t)sk.cells * sizeof(float);
-        if ((rc = ensure(ctx, ctx->sig3, 2 * b)) || (rc = ensure(ctx, ctx->src3, 2 * ctx->S * b)) ||
-            (rc = ensure(ctx, ctx->acc3, 2 * ctx->S * b)) || (rc = ensure(ctx, ctx->ss3, b)) ||
-            (rc = ensure(ctx, ctx->q3, b)))
-            return rc;
-    }
-    void *before[] = {ctx->phi.p,    ctx->src.p,  ctx->part.p, ctx->partials.p, ctx->active.p,
-                      ctx->sig3.p,   ctx->src3.p, ctx->acc3.p, ctx->ss3.p,      ctx->q3.p};
-    if ((rc = ensure(ctx, ctx->phi, state)) || (rc = ensure(ctx, ctx->src, src_bytes)) ||
-        (rc = ensure(ctx, ctx->part, part_units * MOM * cells * sizeof(float))) ||
-        (rc = ensure(ctx, ctx->partials, (size_t)ctx->S * chunks * 2 * sizeof(double))) ||
+    void *before[] = {ctx->phi.p,  ctx->src.p,  ctx->part.p,  ctx->partials.p, ctx->active.p,
+                      ctx->sig3.p, ctx->src3.p, ctx->acc3.p,  ctx->ss3.p,      ctx->q3.p,
+                      ctx->ordsum.p, ctx->dprev.p,
+                      ctx->grow.p, ctx->leak.p, ctx->bal.p, ctx->leak_out.p, ctx->phimin.p,
+                      ctx->sweep_err.p, ctx->otab.p};
+    if ((rc = ensure(ctx, ctx->partials, (size_t)ctx->S * chunks * romk::kNP * sizeof(double))) ||
         (rc = ensure(ctx, ctx->active, ctx->S * sizeof(int))) ||
         (rc = ensure(ctx, ctx->iters, ctx->S * sizeof(int))) ||
         (rc = ensure(ctx, ctx->flags, ctx->S * sizeof(int))) ||
         (rc = ensure(ctx, ctx->resid, ctx->S * sizeof(double))) ||
+        (rc = ensure(ctx, ctx->dprev, ctx->S * sizeof(double))) ||
+        (rc = ensure(ctx, ctx->grow, ctx->S * sizeof(int))) ||
+        (rc = ensure(ctx, ctx->leak, ctx->S * sizeof(double))) ||
+        (rc = ensure(ctx, ctx->bal, ctx->S * sizeof(double))) ||
+        (rc = ensure(ctx, ctx->leak_out, ctx->S * sizeof(double))) ||
+        (rc = ensure(ctx, ctx->phimin, ctx->S * sizeof(double))) ||
+        (rc = ensure(ctx, ctx->ordsum, (size_t)ctx->S * 3 * sizeof(double))) ||
+        (rc = ensure(ctx, ctx->sweep_err, sizeof(int))) ||
         (rc = ensure(ctx, ctx->n_active, sizeof(int))) ||
         (rc = ensure(ctx, ctx->avg, nI * sizeof(double))) ||
         (rc = ensure(ctx, ctx->sum, nI * sizeof(double))))
@@ -1468,51 +1598,19 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     if (ctx->dim == 2 && ctx->opt.tile_g == -1 && ctx->tuned_g == 0) {
         if ((rc = autotune_g(ctx))) return rc;
         if ((rc = build_items(ctx))) return rc;
-        if ((rc = ensure(ctx, ctx->part, part_units * MOM * cells * sizeof(float))))
-            return rc;
         invalidate_graph(ctx);
     }
-    void *after[] = {ctx->phi.p,  ctx->src.p,  ctx->part.p, ctx->partials.p, ctx->active.p,
-                     ctx->sig3.p, ctx->src3.p, ctx->acc3.p, ctx->ss3.p,      ctx->q3.p};
+    if ((rc = ensure_state(ctx))) return rc;
+    void *after[] = {ctx->phi.p,  ctx->src.p,  ctx->part.p,  ctx->partials.p, ctx->active.p,
+                     ctx->sig3.p, ctx->src3.p, ctx->acc3.p,  ctx->ss3.p,      ctx->q3.p,
+                     ctx->ordsum.p, ctx->dprev.p,
+                     ctx->grow.p, ctx->leak.p, ctx->bal.p, ctx->leak_out.p, ctx->phimin.p,
+                     ctx->sweep_err.p, ctx->otab.p};
     if (memcmp(before, after, sizeof before) != 0) invalidate_graph(ctx);
 
     const long long launches0 = ctx->launches;
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
-    if (ctx->MOM == 0 && ctx->opt.dense_precision == 1)
-        CK(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), ctx->stream));
-    if (uses_part(ctx))  // the sweep accumulates; the combine clears it
-        CK(cudaMemsetAsync(ctx->part.p, 0, part_units * MOM * cells * sizeof(float), ctx->stream));
-    if (ctx->dim == 3) {
-        // diagonal storage: sigma_T (both families), the first source q of every
-        // sample, sigma_S and q for the combine (family 0), cleared accumulators, phi = 0
-        const romk::Skew3 sk = romk::make_skew3(ctx->J, ctx->K, ctx->NXP);
-        CK(cudaMemsetAsync(ctx->err3.p, 0, sizeof(int), ctx->stream));
-        CK(cudaMemsetAsync(ctx->acc3.p, 0, 2 * (size_t)ctx->S * sk.cells * sizeof(float),
-                           ctx->stream));
-        CK(romk::launch_skew3_scatter((const float *)ctx->sigt.p, sk, ctx->NXP, 2, 1,
-                                      (float *)ctx->sig3.p, ctx->stream));
-        CK(romk::launch_skew3_scatter((const float *)ctx->q.p, sk, ctx->NXP, 2, ctx->S,
-                                      (float *)ctx->src3.p, ctx->stream));
-        CK(romk::launch_skew3_scatter((const float *)ctx->sigs.p, sk, ctx->NXP, 1, 1,
-                                      (float *)ctx->ss3.p, ctx->stream));
-        CK(romk::launch_skew3_scatter((const float *)ctx->q.p, sk, ctx->NXP, 1, 1,
-                                      (float *)ctx->q3.p, ctx->stream));
-        ctx->launches += 4;
-        CK(romk::launch_init_state(ctx->S, 1, sk.cells, nullptr, (float *)ctx->phi.p, nullptr,
-                                   (int *)ctx->active.p, (int *)ctx->iters.p, (int *)ctx->flags.p,
-                                   (double *)ctx->resid.p, ctx->stream));
-    } else {
-        CK(romk::launch_init_state(ctx->S, MOM, cells, (const float *)ctx->q.p,
-                                   (float *)ctx->phi.p, (float *)ctx->src.p, (int *)ctx->active.p,
-                                   (int *)ctx->iters.p, (int *)ctx->flags.p,
-                                   (double *)ctx->resid.p, ctx->stream));
-    }
-    ++ctx->launches;
-    if (ctx->MOM == 0) {  // psi^0 = 0: every ordinate's first source is q
-        CK(romk::launch_dense_init((const float *)ctx->q.p, cells, ctx->Mtot,
-                                   (float *)ctx->src_ord.p, ctx->stream));
-        ++ctx->launches;
-    }
+    if ((rc = init_state(ctx))) return rc;
     const int cap = ctx->opt.fixed_iters > 0 ? ctx->opt.fixed_iters : ctx->opt.max_iter;
     const bool timed = ctx->opt.time_kernels == 1;
     double sweep_ms = 0.0, source_ms = 0.0;
@@ -1573,10 +1671,21 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     ctx->h_iters.assign(ctx->S, 0);
     ctx->h_resid.assign(ctx->S, 0.0);
+    ctx->h_bal.assign(ctx->S, 0.0);
+    ctx->h_leak.assign(ctx->S, 0.0);
+    ctx->h_phimin.assign(ctx->S, 0.0);
     std::vector<int> flags(ctx->S, 0);
-    int err3 = 0, tc_err = 0;
+    int err3 = 0, tc_err = 0, sweep_err = 0;
     if (ctx->dim == 3)
         CK(cudaMemcpyAsync(&err3, ctx->err3.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&sweep_err, ctx->sweep_err.p, sizeof(int), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_bal.data(), ctx->bal.p, ctx->S * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_leak.data(), ctx->leak_out.p, ctx->S * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_phimin.data(), ctx->phimin.p, ctx->S * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->stream));
     if (ctx->MOM == 0 && ctx->opt.dense_precision == 1)
         CK(cudaMemcpyAsync(&tc_err, ctx->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost,
                            ctx->stream));
@@ -1590,9 +1699,13 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
     if (err3)
-        return fail(ctx, ROM_ERR_CUDA, "3D sweep: a wait between warps timed out (flags %d)", err3);
+        return fail(ctx, ROM_ERR_TIMEOUT, "3D sweep: a wait between warps timed out (flags %d)",
+                    err3);
+    if (sweep_err)
+        return fail(ctx, ROM_ERR_TIMEOUT, "X-Y sweep: a bounded wait ran out (flags %d)",
+                    sweep_err);
     if (tc_err)
-        return fail(ctx, ROM_ERR_CUDA, "tensor-core dense source: a wait timed out (flags %d)",
+        return fail(ctx, ROM_ERR_TIMEOUT, "tensor-core dense source: a wait timed out (flags %d)",
                     tc_err);
     ctx->solved = true;
 
@@ -1600,7 +1713,9 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     st.n_samples = ctx->S;
     st.iterations_max = 0;
     st.iterations_min = ctx->S ? ctx->h_iters[0] : 0;
-    int diverged = 0;
+    int diverged = 0, growing = 0;
+    st.balance_max = has_balance(ctx) ? 0.0 : NAN;
+    st.phi_min = INFINITY;
     for (int s = 0; s < ctx->S; ++s) {
         const int it = ctx->h_iters[s];
         st.iterations_max = std::max(st.iterations_max, it);
@@ -1608,8 +1723,14 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
         st.updates += (int64_t)n_cells(ctx) * ctx->M[s] * it;
         const double r = ctx->h_resid[s];
         if (!(r <= st.residual_max)) st.residual_max = r;
-        if (flags[s] & 1) ++diverged;
-        else if (ctx->opt.fixed_iters == 0 && !(r < ctx->opt.tol)) ++st.n_not_converged;
+        if (has_balance(ctx) && !(ctx->h_bal[s] <= st.balance_max)) st.balance_max = ctx->h_bal[s];
+        st.phi_min = std::min(st.phi_min, ctx->h_phimin[s]);
+        if (flags[s] & 3) {
+            ++diverged;
+            if (flags[s] & 2) ++growing;
+        } else if (ctx->opt.fixed_iters == 0 && !(r < ctx->opt.tol)) {
+            ++st.n_not_converged;
+        }
     }
     st.gpu_ms = ms;
     st.sweep_ms = sweep_ms;
@@ -1621,7 +1742,11 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     if (device_loop) ctx->launches += (long long)launches_per_iteration(ctx) * st.iterations_max;
     st.kernel_launches = ctx->launches - launches0;
     if (stats_out) *stats_out = st;
-    if (diverged) return fail(ctx, ROM_ERR_DIVERGED, "%d samples diverged (NaN/Inf residual)", diverged);
+    if (diverged)
+        return fail(ctx, ROM_ERR_DIVERGED,
+                    "%d samples diverged (%d with a NaN/Inf residual, %d with a change that grew "
+                    "for %d sweeps)",
+                    diverged, diverged - growing, growing, ctx->opt.diverge_window);
     if (st.n_not_converged)
         return fail(ctx, ROM_ERR_NOT_CONVERGED, "%d samples did not reach tol %g in %d sweeps",
                     st.n_not_converged, ctx->opt.tol, ctx->opt.max_iter);
@@ -1685,6 +1810,19 @@ int rom_get_iterations(rom_ctx *ctx, int32_t *iters, double *residuals)
     for (int s = 0; s < ctx->S; ++s) {
         if (iters) iters[s] = ctx->h_iters[s];
         if (residuals) residuals[s] = ctx->h_resid[s];
+    }
+    return ROM_OK;
+}
+
+int rom_get_balance(rom_ctx *ctx, double *leakage, double *balance, double *phi_min)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    if (!ctx->solved) return fail(ctx, ROM_ERR_STATE, "call rom_solve first");
+    const bool have = has_balance(ctx);
+    for (int s = 0; s < ctx->S; ++s) {
+        if (leakage) leakage[s] = have ? ctx->h_leak[s] : NAN;
+        if (balance) balance[s] = have ? ctx->h_bal[s] : NAN;
+        if (phi_min) phi_min[s] = ctx->h_phimin[s];
     }
     return ROM_OK;
 }

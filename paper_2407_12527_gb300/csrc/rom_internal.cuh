@@ -24,6 +24,11 @@ constexpr int kMaxG = 4;       // ordinates per sweep work item
 constexpr int kMaxWarps = 8;   // I <= 32 * 8 * 8 = 2048
 constexpr int kMaxCtaItems3 = 256;  // 3D: work items per CTA list
 
+// Partials per (sample, combine block), FP64: squared change and squared norm
+// of phi (residual), sum of sigma_T phi, sums of the three source moments of
+// the previous iterate (balance), min phi.
+constexpr int kNP = 7;
+
 // One sweep work item: up to kMaxG ordinates of one quadrant of one sample.
 // quad bit 0 set: c < 0 (sweep from x_R), bit 1 set: s < 0 (sweep from y_T),
 // bit 2 set (3D): mu_z < 0 (sweep from z_T).
@@ -50,20 +55,31 @@ struct SweepArgs {
     long long inflow_stride;    // per ordinate (0 = same values for every ordinate)
     const int *active;          // [S] samples still iterating
     long long cells;            // J * NXP
+    // moment modes: the net leakage of each sample's sweep (nullptr: not kept)
+    double *leak;               // [S]
+    float dx, dy;               // leakage weights |c| dy, |s| dx
+    int *err;                   // bit 0: the test hook's wait ran out
+    unsigned long long wait_ns; // bound of that wait
+    int stall;                  // test hook: every warp waits on a barrier nothing completes
 };
 // The X-Y sweep adds the moments of every work item to part[sample] (vector
 // reductions; the combine reads and clears them).
 
 struct CombineArgs {
     int S, MOM, chunks;
+    int I, NXP;                 // columns and row pitch (min phi skips padding columns)
     long long cells;
     float g;                    // linear-kernel asymmetry (MOM = 3)
     float *acc;                 // [S][MOM][cells] moments added by the sweep, cleared here
     float *phi;
     float *src;
     const float *sigma_s, *q;
+    // balance partials (moment modes): sigma_T per cell, nullptr = sigma_t_homog
+    int balance;
+    const float *sigma_t;
+    float sigma_t_homog;
     const int *active;
-    double *partials;           // [S][chunks][2]
+    double *partials;           // [S][chunks][kNP]
 };
 
 // Diagonal storage of 3D cell arrays read or written by the sweep (source, sigma_T,
@@ -122,20 +138,38 @@ struct Sweep3Args {
     int n_tx, n_ty;             // tiles along x and y
     float *xface;               // [items][G][K][J] x-edges handed to the next x tile
     float *yface;               // [items][G][K][NXP] y-edges handed to the next y tile
-    int *err;                   // bit 0/1: an mbarrier wait timed out
+    int *err;                   // bit 0/1: an mbarrier wait timed out (bit 2: the test hook's)
+    unsigned long long wait_ns; // bound of every wait
+    int stall;                  // test hook: every warp waits on a barrier nothing completes
 };
 
 struct FinalizeArgs {
     int S, chunks;
     int fixed_iters, max_iter;
     double tol;
-    const double *partials;
+    int diverge_window;         // stop a sample after this many sweeps of growing change (0: off)
+    const double *partials;     // [S][chunks][kNP]
     int *active, *iters, *flags;
     double *resid;
+    double *dprev;              // [S] ||phi^k - phi^{k-1}||_2 of the previous sweep
+    int *grow;                  // [S] consecutive sweeps whose change grew
+    // particle balance of the sweep (balance != 0): the net leakage the sweep
+    // added per sample (read and cleared), the cell area and per-sample sums
+    // sum_l w_l, sum_l w_l c_l, sum_l w_l s_l ([S][3])
+    int balance;
+    double *leak;
+    double dA;
+    const double *ordsum;
+    double *bal_out, *leak_out, *phimin_out;  // [S] values of each sample's last sweep
     int *n_active;
     int use_cond;
     cudaGraphConditionalHandle cond;
 };
+
+// per-sample FP64 sums sum_l w_l, sum_l w_l c_l, sum_l w_l s_l -> out [S][3]
+cudaError_t launch_ordsum(const double *c, const double *s, const double *w,
+                          const long long *ord_off, const int *M, int S, double *out,
+                          cudaStream_t st);
 
 // Ordinate generation (one thread per quadrant-1 cell of a sample).
 struct OrdGenArgs {
@@ -253,13 +287,14 @@ cudaError_t launch_combine(const CombineArgs &a, cudaStream_t st);
 // source sigma_S phi + q in both diagonal families; phi, sigma_S, q in family 0.
 struct Combine3Args {
     int S, chunks;
+    int I;                      // columns (min phi skips padding columns)
     Skew3 sk;
     float *acc;                 // [2][S][sk.cells], cleared after reading
     float *src;                 // [2][S][sk.cells]
     float *phi;                 // [S][sk.cells] (family 0)
     const float *sigma_s, *q;   // [sk.cells] (family 0)
     const int *active;
-    double *partials;           // [S][chunks][2]
+    double *partials;           // [S][chunks][kNP]
 };
 cudaError_t launch_combine3(const Combine3Args &a, cudaStream_t st);
 cudaError_t launch_average3(const float *phi, int S, const Skew3 &sk, int I, double *avg,
@@ -274,6 +309,10 @@ cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t st);
 cudaError_t launch_init_state(int S, int MOM, long long cells, const float *q, float *phi,
                               float *src, int *active, int *iters, int *flags, double *resid,
                               cudaStream_t st);
+// per-sample divergence and balance state of a new solve: dprev = +inf, grow = 0,
+// leak = 0, bal / leak_out / phimin = NaN
+cudaError_t launch_init_checks(int S, double *dprev, int *grow, double *leak, double *bal,
+                               double *leak_out, double *phimin, cudaStream_t st);
 cudaError_t launch_average(const float *phi, int S, int MOM, int I, int J, int NXP, double *avg,
                            double *sum, cudaStream_t st);
 cudaError_t launch_extract(const float *phi, int sample, int MOM, int I, int J, int NXP,

@@ -40,6 +40,48 @@ __device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float2 add_(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float neg_(float a) { return -a; }
 __device__ __forceinline__ float2 neg_(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float2 sub_(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+// Compensated (Kahan) FP32 sum of the boundary terms of the leakage: one term per
+// step on the boundary lanes, a few ulps of the total instead of n ulps; widened to
+// FP64 once per lane.
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// mbarrier helpers of the test hook (a bounded wait on a barrier nothing completes)
+__device__ __forceinline__ unsigned smem_u32a(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ bool never_wait(unsigned long long *b, unsigned long long budget_ns)
+{
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32a(b)), "r"(0u)
+            : "memory");
+        if (__all_sync(0xffffffffu, ok != 0)) return true;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (__any_sync(0xffffffffu, t - t0 > budget_ns)) return false;
+    }
+}
 // 1 / (sigma_T + a + b) of a cell with varying sigma_T: the hardware reciprocal
 // (rcp.approx, within 1 ulp; the argument is >= sigma_T > 0, never subnormal)
 __device__ __forceinline__ float rcp_(float a)
@@ -132,6 +174,7 @@ struct OrdPacks {
     //         psi_c  = (x + x_out) / 2
     //   step: psi_c  = ar x + rd (S + b py) = x_out = py_out,  ar = a rd, br = b rd
     T al[N], a2[N], b2[N], be[N], r2[N], wh[N], ar[N], br[N];
+    T lx[N], ly[N];  // leakage weights w |c| dy and w |s| dx
     int ord[G];
 };
 
@@ -237,19 +280,19 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &A, int blk, bool yn
                     }
                 }
                 if (HOMOG && SCHEME == 0) {
-                    const T s2 = mul_(S, o.r2[p]);                 // 2 rd S
-                    const T xn = fma_(o.al[p], x[p], fma_(o.b2[p], py[r][p], s2));
-                    const T pyn = fma_(o.a2[p], x[p], fma_(o.be[p], py[r][p], s2));
-                    if (MOM == 0) psi_put(psi_row, p, r, mul_(add_(x[p], xn), splat<T>(0.5f)));
+                    // x_out = al x + b2 py + 2 rd S; sum = x + x_out = 2 psi_c;
+                    // py_out = sum - py (the DD closure), w psi_c = (w / 2) sum
+                    const T xn = fma_(o.al[p], x[p], fma_(o.b2[p], py[r][p], mul_(S, o.r2[p])));
+                    const T sm = add_(x[p], xn);
+                    if (MOM == 0) psi_put(psi_row, p, r, mul_(sm, splat<T>(0.5f)));
                     if (ok) {
-                        acc0[r] = fma_(o.wh[p], add_(x[p], xn), acc0[r]);
+                        acc0[r] = fma_(o.wh[p], sm, acc0[r]);
                         if (MOM == 3) {
-                            const T sm = add_(x[p], xn);
                             acc1[r] = fma_(mul_(o.wc[p], splat<T>(0.5f)), sm, acc1[r]);
                             acc2[r] = fma_(mul_(o.ws[p], splat<T>(0.5f)), sm, acc2[r]);
                         }
+                        py[r][p] = sub_(sm, py[r][p]);
                         x[p] = xn;
-                        py[r][p] = pyn;
                     }
                 } else if (HOMOG) {
                     const T pc = fma_(o.ar[p], x[p], fma_(o.br[p], py[r][p], mul_(S, o.rd[p])));
@@ -354,6 +397,17 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
                              col0 + r];
             setc(py[r][G == 1 ? 0 : k >> 1], G == 1 ? 0 : k & 1, v);
         }
+    // net leakage of the item (moment modes): sum_l w_l (|c_l| dy sum_rows +
+    // |s_l| dx sum_cols) (psi_out - psi_in), Kahan-summed per lane
+    Kahan leak;
+    if (A.leak && lane_on) {
+        float lin = 0.f;
+#pragma unroll
+        for (int r = 0; r < kCols; ++r)
+#pragma unroll
+            for (int p = 0; p < N; ++p) lin += hsum(mul_(o.ly[p], py[r][p]));
+        leak.add(-lin);
+    }
 
     T xin[kH][N];
 #pragma unroll
@@ -406,6 +460,14 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
                         }
                         setc(xin[h][G == 1 ? 0 : k >> 1], G == 1 ? 0 : k & 1, v);
                     }
+                if (A.leak) {  // rows past J carry zero inflow
+                    float lin = 0.f;
+#pragma unroll
+                    for (int h = 0; h < kH; ++h)
+#pragma unroll
+                        for (int p = 0; p < N; ++p) lin += hsum(mul_(o.lx[p], xin[h][p]));
+                    leak.add(-lin);
+                }
             }
             const bool full = full_cols && (blk + 1) * kH <= A.J;
             if (full)
@@ -414,6 +476,14 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
             else
                 sweep_block<G, MOM, SCHEME, HOMOG, XNEG, true, STORE_LATE>(
                     A, blk, yneg, col0, o, py, xin, xo, cur, out, part_i);
+            if (A.leak && d == L - 1) {  // the outflow x face; rows past J leave zeros
+                float lo = 0.f;
+#pragma unroll
+                for (int h = 0; h < kH; ++h)
+#pragma unroll
+                    for (int p = 0; p < N; ++p) lo += hsum(mul_(o.lx[p], xo[h][p]));
+                leak.add(lo);
+            }
         } else {
 #pragma unroll
             for (int h = 0; h < kH; ++h)
@@ -472,6 +542,21 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
     } else {
         for (int t = 0; t < T_steps; ++t) step(t, buf[0], buf[0]);
     }
+    if (A.leak) {  // outgoing y-edges of the lane's columns, then one FP64 add per warp
+        if (lane_on) {
+            float lo = 0.f;
+#pragma unroll
+            for (int r = 0; r < kCols; ++r)
+                if (col0 + r < A.I)
+#pragma unroll
+                    for (int p = 0; p < N; ++p) lo += hsum(mul_(o.ly[p], py[r][p]));
+            leak.add(lo);
+        }
+        double lk = leak.value();
+#pragma unroll
+        for (int dd = 16; dd > 0; dd >>= 1) lk += __shfl_xor_sync(0xffffffffu, lk, dd);
+        if ((g & 31) == 0 && lk != 0.0) atomicAdd(A.leak + it.sample, lk);
+    }
 }
 
 template <int G, int MOM, int SCHEME, bool HOMOG>
@@ -479,6 +564,16 @@ __global__ void __launch_bounds__(32 * kMaxWarps) sweep2d_kernel(const SweepArgs
 {
     const SweepItem it = A.items[blockIdx.x];
     if (!A.active[it.sample]) return;
+    if (A.stall) {  // test hook: every warp waits on a barrier that nothing completes
+        __shared__ unsigned long long never;
+        if (threadIdx.x == 0)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32a(&never)) : "memory");
+        __syncthreads();
+        if (!never_wait(&never, A.wait_ns)) {
+            if ((threadIdx.x & 31) == 0) atomicOr(A.err, 1);
+            return;
+        }
+    }
     OrdPacks<G> o;
     const float f = SCHEME == 0 ? 2.f : 1.f;
 #pragma unroll
@@ -512,6 +607,8 @@ __global__ void __launch_bounds__(32 * kMaxWarps) sweep2d_kernel(const SweepArgs
         setc(o.wh[p], i, 0.5f * w);
         setc(o.ar[p], i, a * rd);
         setc(o.br[p], i, b * rd);
+        setc(o.lx[p], i, w * fabsf(c) * A.dy);
+        setc(o.ly[p], i, w * fabsf(s) * A.dx);
     }
     if (it.quad & 1)
         sweep_item<G, MOM, SCHEME, HOMOG, true>(A, it, o);

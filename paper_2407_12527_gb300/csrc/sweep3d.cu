@@ -38,8 +38,8 @@
 // With 255 registers per thread a CTA is 8 warps, one per SM.  Wider x-y
 // extents are cut into tiles swept by successive launches in upwind order; a
 // tile hands its downstream x- and y-edges to the next tile through per-item
-// face buffers.  Every mbarrier wait is bounded: on timeout the kernel raises
-// an error flag and returns.
+// face buffers.  Every mbarrier wait is bounded in time (globaltimer): on
+// timeout the kernel raises an error flag and returns.
 #include "rom_internal.cuh"
 
 namespace romk {
@@ -49,12 +49,12 @@ constexpr int kH3 = 4;                  // rows per lane
 constexpr int kStrips = 8;              // 8-column strips (warps) per tile: 64 columns
 constexpr int kTileRows = 32 * kH3;     // 128 rows per tile
 constexpr int kSlots = 4;               // x-edge ring depth between neighbouring warps
-constexpr unsigned kWaitTries = 1u << 21;  // bounded mbarrier wait (x ~1 us hint)
 
 struct Smem3 {
     float4 ring[kStrips][kSlots][32][2];  // 4 rows x up to 2 ordinates per lane
     unsigned long long full[kStrips][kSlots];
     unsigned long long empty[kStrips][kSlots];
+    unsigned long long never;  // test hook: a barrier no thread arrives on
     int sample[kMaxCtaItems3];
     int ord[kMaxCtaItems3][2];
     int item[kMaxCtaItems3];
@@ -132,12 +132,23 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned pa
         : "memory");
     return ok != 0;
 }
-// Wait (all lanes of the warp together) for the phase of `parity` to complete.
-__device__ __forceinline__ bool wait_warp(unsigned long long *b, unsigned parity)
+__device__ __forceinline__ unsigned long long gtimer_ns()
 {
-    for (unsigned i = 0; i < kWaitTries; ++i)
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait (all lanes of the warp together) for the phase of `parity` to complete,
+// for at most budget_ns nanoseconds (the decision to give up is warp-uniform).
+__device__ __forceinline__ bool wait_warp(unsigned long long *b, unsigned parity,
+                                          unsigned long long budget_ns)
+{
+    if (__all_sync(0xffffffffu, mbar_try_wait(b, parity))) return true;
+    const unsigned long long t0 = gtimer_ns();
+    for (;;) {
         if (__all_sync(0xffffffffu, mbar_try_wait(b, parity))) return true;
-    return false;
+        if (__any_sync(0xffffffffu, gtimer_ns() - t0 > budget_ns)) return false;
+    }
 }
 
 __device__ __forceinline__ void red8(float *p, const float (&v)[kCols])
@@ -343,7 +354,7 @@ __device__ __forceinline__ void sweep3_body(const Sweep3Args &A, Smem3 &sm, int 
                     }
             }
         } else {
-            if (!wait_warp(&sm.full[w - 1][slot], par)) {
+            if (!wait_warp(&sm.full[w - 1][slot], par, A.wait_ns)) {
                 if (lane == 0) atomicOr(A.err, 1);
                 return;
             }
@@ -416,7 +427,7 @@ __device__ __forceinline__ void sweep3_body(const Sweep3Args &A, Smem3 &sm, int 
                                 vget(xo[h], g);
             }
         } else {
-            if (t >= kSlots && !wait_warp(&sm.empty[w][slot], par ^ 1u)) {
+            if (t >= kSlots && !wait_warp(&sm.empty[w][slot], par ^ 1u, A.wait_ns)) {
                 if (lane == 0) atomicOr(A.err, 2);
                 return;
             }
@@ -486,9 +497,16 @@ __global__ void __launch_bounds__(32 * kStrips, 1) sweep3d_kernel(const Sweep3Ar
             mbar_init(&sm.full[i / kSlots][i % kSlots], 32);
             mbar_init(&sm.empty[i / kSlots][i % kSlots], 32);
         }
+        if (lane == 0) mbar_init(&sm.never, 1);
     }
     __syncthreads();
     if (sm.n_list == 0) return;
+    if (A.stall) {  // test hook: wait for a phase that never completes
+        if (!wait_warp(&sm.never, 0u, A.wait_ns)) {
+            if ((threadIdx.x & 31) == 0) atomicOr(A.err, 4);
+            return;
+        }
+    }
     const int oct = A.items[sm.item[0]].quad;
     if (oct & 1) sweep3_body<G, SCHEME, true>(A, sm, oct);
     else sweep3_body<G, SCHEME, false>(A, sm, oct);

@@ -20,7 +20,7 @@ LIB_PATH = PKG / "librom_gb300.so"
 
 ROM_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "NOT_CONVERGED", -5: "DIVERGED",
-          -6: "STATE", -7: "UNSUPPORTED"}
+          -6: "STATE", -7: "UNSUPPORTED", -8: "TIMEOUT"}
 SCHEME = {"dd": 0, "step": 1}
 KERNEL = {"iso": 0, "linear": 1, "hg": 2}
 KERNEL_FLAG_NORMALIZE = 1
@@ -34,7 +34,9 @@ class rom_options(ctypes.Structure):
                 ("fixed_iters", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("tile_g", ctypes.c_int), ("time_kernels", ctypes.c_int),
                 ("dense_source", ctypes.c_int), ("dense_precision", ctypes.c_int),
-                ("rows_per_step", ctypes.c_int)]
+                ("rows_per_step", ctypes.c_int),
+                ("diverge_window", ctypes.c_int), ("wait_timeout_ms", ctypes.c_double),
+                ("test_stall_waits", ctypes.c_int)]
 
 
 class rom_stats(ctypes.Structure):
@@ -44,7 +46,9 @@ class rom_stats(ctypes.Structure):
                 ("gpu_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("sweep_ms", ctypes.c_double), ("sweep_launches", ctypes.c_int64),
                 ("source_ms", ctypes.c_double), ("source_launches", ctypes.c_int64),
-                ("tile_g", ctypes.c_int), ("rows_per_step", ctypes.c_int)]
+                ("tile_g", ctypes.c_int), ("rows_per_step", ctypes.c_int),
+                ("balance_max", ctypes.c_double),
+                ("phi_min", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +93,7 @@ SIGNATURES = {
     "rom_get_scalar_flux_device": (_i, [_vp, _i, _vp]),
     "rom_get_iterations": (_i, [_vp, _i32p, _dp]),
     "rom_get_partial_sum": (_i, [_vp, _dp, _i64p]),
+    "rom_get_balance": (_i, [_vp, _dp, _dp, _dp]),
     "rom_sweep_xy_noalloc": (_i, [_vp, _i, _i, ctypes.c_double, ctypes.c_double, _i, _vp, _i,
                                   _i32p, _dp, _dp, _vp, _vp, ctypes.c_char_p, ctypes.c_size_t]),
 }
@@ -312,6 +317,15 @@ class RomContext:
         self._check(self.L.rom_get_iterations(self.h, _ptr(it, _i32p), _ptr(r)),
                     "rom_get_iterations")
         return it, r
+
+    def balance(self):
+        """(net leakage, relative balance error, min phi) of each sample's last sweep."""
+        lk = np.zeros(self.n_samples)
+        bal = np.zeros(self.n_samples)
+        mn = np.zeros(self.n_samples)
+        self._check(self.L.rom_get_balance(self.h, _ptr(lk), _ptr(bal), _ptr(mn)),
+                    "rom_get_balance")
+        return lk, bal, mn
 
     def partial_sum(self):
         s = np.zeros(self._shape())

@@ -14,6 +14,7 @@ import pytest
 
 from oracle import oracle as O
 import rom_workloads as W
+from parity_util import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -30,8 +31,6 @@ def rom():
     return R
 
 
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
 def gpu_solve(R, I, J, bounds, st, ss, q, seed, nz, nt, kernel="hg", g=0.8, flags=0, **opts):

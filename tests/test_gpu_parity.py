@@ -14,6 +14,7 @@ import pytest
 
 from oracle import oracle as O
 import rom_workloads as W
+from parity_util import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -30,8 +31,6 @@ def rom():
     return R
 
 
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
 def gpu_solve(R, I, J, bounds, st, ss, q, sets=None, seed=None, nz=None, nt=None, kernel="iso",
@@ -103,8 +102,11 @@ GRIDS = [
 @pytest.mark.parametrize("grid", GRIDS, ids=[f"{g[0]}x{g[1]}" for g in GRIDS])
 @pytest.mark.parametrize("homog", [True, False])
 @pytest.mark.parametrize("rows", [4, 2])
-def test_fixed_k_parity_random_directions(rom, scheme, grid, homog, rows):
-    """Rows = grid rows a lane advances per wavefront step (both kernel shapes)."""
+@pytest.mark.parametrize("tile_g", [1, 2, 4])
+def test_fixed_k_parity_random_directions(rom, scheme, grid, homog, rows, tile_g):
+    """rows = grid rows a lane advances per wavefront step, tile_g = ordinates per
+    work item (every compiled kernel shape); ragged grids leave a partial lane and
+    partial row blocks, and a 300-wide grid spans two warps."""
     I, J, bounds = grid
     st, ss, q = W.random_medium(I, J, seed=I * 31 + J)
     if homog:
@@ -114,12 +116,13 @@ def test_fixed_k_parity_random_directions(rom, scheme, grid, homog, rows):
             for M in (5, 12, 3)]
     K = 4
     gpu = gpu_solve(rom, I, J, bounds, st, ss, q, sets=sets, scheme=rom.SCHEME[scheme],
-                    fixed_iters=K, rows_per_step=rows)
+                    fixed_iters=K, rows_per_step=rows, tile_g=tile_g)
     ref = O.solve_xy(I, J, bounds, st, ss, q, sets, scheme=scheme, fixed_iters=K)
     for k in range(len(sets)):
         assert rel(gpu["phi"][k], ref["phi"][k]) < TOL, k
     assert list(gpu["iters"]) == [K] * len(sets)
     assert gpu["stats"]["rows_per_step"] == rows
+    assert gpu["stats"]["tile_g"] == tile_g
 
 
 @pytest.mark.parametrize("tile_g", [-1, 1, 2, 4])

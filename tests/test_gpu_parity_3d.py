@@ -10,6 +10,7 @@ import pytest
 
 from oracle import oracle as O
 import rom_workloads as W
+from parity_util import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -26,8 +27,6 @@ def rom():
     return R
 
 
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
 def gpu_solve3(R, I, J, K, bounds, st, ss, q, sets=None, seed=None, nz=None, nt=None,
