@@ -33,11 +33,12 @@
 namespace romk {
 namespace {
 
-// The block's partials: six FP32 per-thread sums (squared change, squared
-// norm, sigma_T phi, three source moments) and a min, summed by an FP32 warp
-// tree, then in FP64 across the warps; written to out[0 .. kNP-1].  Every
-// thread of the block calls it.
-__device__ __forceinline__ void block_partials(float (&v)[6], float mn, double *out)
+// The block's contribution to its sample's sums: six FP32 per-thread sums
+// (squared change, squared norm, sigma_T phi, three source moments) and a min,
+// reduced by an FP32 warp tree, then in FP64 across the warps, and added to the
+// sample's FP64 sums with one atomic per value (the min by an atomic min on the
+// ordered-int key).  Every thread of the block calls it.
+__device__ __forceinline__ void block_partials(float (&v)[6], float mn, double *sums, int *minkey)
 {
     __shared__ double red[6][32];
     __shared__ float redm[32];
@@ -57,11 +58,11 @@ __device__ __forceinline__ void block_partials(float (&v)[6], float mn, double *
     if (threadIdx.x < 6) {
         double acc = 0.0;
         for (int k = 0; k < nw; ++k) acc += red[threadIdx.x][k];
-        out[threadIdx.x] = acc;
+        if (acc != 0.0) atomicAdd(sums + threadIdx.x, acc);
     } else if (threadIdx.x == 6) {
         float m = redm[0];
         for (int k = 1; k < nw; ++k) m = fminf(m, redm[k]);
-        out[6] = (double)m;
+        if (m < INFINITY) atomicMin(minkey, float_order_key(m));
     }
 }
 
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
         }
     }
     float v6[6] = {d2f, n2f, a1f, b0f, b1f, b2f};
-    block_partials(v6, mn, A.partials + ((long long)s * A.chunks + blockIdx.x) * kNP);
+    block_partials(v6, mn, A.sums + (long long)s * kNP, A.minkey + s);
 }
 
 // 3D: phi of each sample from its two diagonal-storage accumulators (read and
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(256) combine3_kernel(const Combine3Args A)
         stg8(src1 + i1, out);
     }
     float v6[6] = {d2f, n2f, 0.f, 0.f, 0.f, 0.f};
-    block_partials(v6, mn, A.partials + ((long long)s * A.chunks + blockIdx.x) * kNP);
+    block_partials(v6, mn, A.sums + (long long)s * kNP, A.minkey + s);
 }
 
 // 3D average / extraction from family-0 diagonal storage [S][sk.cells] into [K][J][I]
@@ -251,17 +252,14 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalizeArgs A)
     int cnt = 0;
     for (int s = threadIdx.x; s < A.S; s += blockDim.x) {
         if (!A.active[s]) continue;
-        double d2 = 0.0, n2 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, mn = INFINITY;
-        for (int c = 0; c < A.chunks; ++c) {
-            const double *p = A.partials + ((long long)s * A.chunks + c) * kNP;
-            d2 += p[0];
-            n2 += p[1];
-            a1 += p[2];
-            b0 += p[3];
-            b1 += p[4];
-            b2 += p[5];
-            mn = fmin(mn, p[6]);
-        }
+        // the sums the combine blocks added, cleared for the next sweep
+        double *sm = A.sums + (long long)s * kNP;
+        const double d2 = sm[0], n2 = sm[1], a1 = sm[2], b0 = sm[3], b1 = sm[4], b2 = sm[5];
+#pragma unroll
+        for (int k = 0; k < kNP; ++k) sm[k] = 0.0;
+        const int mk = A.minkey[s];
+        A.minkey[s] = 0x7FFFFFFF;
+        const double mn = mk == 0x7FFFFFFF ? (double)NAN : (double)float_from_order_key(mk);
         const double r = n2 > 0.0 ? sqrt(d2 / n2) : (d2 == 0.0 ? 0.0 : (double)INFINITY);
         const int it = A.iters[s] + 1;
         A.iters[s] = it;
@@ -309,7 +307,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalizeArgs A)
 }
 
 __global__ void init_checks_kernel(int S, double *dprev, int *grow, double *leak, double *bal,
-                                   double *leak_out, double *phimin)
+                                   double *leak_out, double *phimin, double *sums, int *minkey)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
@@ -319,6 +317,9 @@ __global__ void init_checks_kernel(int S, double *dprev, int *grow, double *leak
     bal[s] = (double)NAN;
     leak_out[s] = (double)NAN;
     phimin[s] = (double)NAN;
+#pragma unroll
+    for (int k = 0; k < kNP; ++k) sums[(long long)s * kNP + k] = 0.0;
+    minkey[s] = 0x7FFFFFFF;
 }
 
 __global__ void ordsum_kernel(const double *c, const double *s, const double *w,
@@ -520,10 +521,11 @@ cudaError_t launch_ordsum(const double *c, const double *s, const double *w,
 }
 
 cudaError_t launch_init_checks(int S, double *dprev, int *grow, double *leak, double *bal,
-                               double *leak_out, double *phimin, cudaStream_t st)
+                               double *leak_out, double *phimin, double *sums, int *minkey,
+                               cudaStream_t st)
 {
     init_checks_kernel<<<(S + 255) / 256, 256, 0, st>>>(S, dprev, grow, leak, bal, leak_out,
-                                                        phimin);
+                                                        phimin, sums, minkey);
     return cudaGetLastError();
 }
 

@@ -6,7 +6,7 @@
 // Source iteration (Sec. 3.2, eq. psiexpansion), per sweep k:
 //   sweep    (K1; K9 on 3D grids) every active sample: moments of
 //                  L^{-1}(scatter(psi^{k-1}) + q)
-//   combine  (K2)  phi^k per sample, next source, FP64 residual partials
+//   combine  (K2)  phi^k per sample, next source, FP64 residual and balance sums
 //   finalize (K5)  ||phi^k - phi^{k-1}|| / ||phi^k|| per sample, stop flags
 // then the FP64 sample average (K6).  The loop runs either on the device (a
 // CUDA graph whose conditional while-node repeats the three kernels until no
@@ -120,7 +120,7 @@ struct rom_ctx {
     // iteration state
     int MOM = 1;  // 1 isotropic moments, 3 linear moments, 0 dense operator
     int chunks = 1;
-    DevBuf phi, src, part, partials, active, iters, flags, resid, n_active, avg, sum, tmp;
+    DevBuf phi, src, part, sums, minkey, active, iters, flags, resid, n_active, avg, sum, tmp;
     bool solved = false;
     std::vector<int> h_iters;
     std::vector<double> h_resid;
@@ -775,7 +775,8 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     ca.sigma_s = (const float *)ctx->sigs.p;
     ca.q = (const float *)ctx->q.p;
     ca.active = (const int *)ctx->active.p;
-    ca.partials = (double *)ctx->partials.p;
+    ca.sums = (double *)ctx->sums.p;
+    ca.minkey = (int *)ctx->minkey.p;
     ca.balance = has_balance(ctx) ? 1 : 0;
     ca.sigma_t = ctx->homog ? nullptr : (const float *)ctx->sigt.p;
     ca.sigma_t_homog = ctx->sigma_t_homog;
@@ -790,7 +791,8 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
         c3.sigma_s = (const float *)ctx->ss3.p;
         c3.q = (const float *)ctx->q3.p;
         c3.active = (const int *)ctx->active.p;
-        c3.partials = (double *)ctx->partials.p;
+        c3.sums = (double *)ctx->sums.p;
+        c3.minkey = (int *)ctx->minkey.p;
         c3.I = ctx->I;
         CK(romk::launch_combine3(c3, st));
     } else {
@@ -822,7 +824,8 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     fa.fixed_iters = ctx->opt.fixed_iters;
     fa.max_iter = ctx->opt.max_iter;
     fa.tol = ctx->opt.tol;
-    fa.partials = (const double *)ctx->partials.p;
+    fa.sums = (double *)ctx->sums.p;
+    fa.minkey = (int *)ctx->minkey.p;
     fa.active = (int *)ctx->active.p;
     fa.iters = (int *)ctx->iters.p;
     fa.flags = (int *)ctx->flags.p;
@@ -967,7 +970,8 @@ int init_state(rom_ctx *ctx)
     }
     CK(romk::launch_init_checks(ctx->S, (double *)ctx->dprev.p, (int *)ctx->grow.p,
                                 (double *)ctx->leak.p, (double *)ctx->bal.p,
-                                (double *)ctx->leak_out.p, (double *)ctx->phimin.p, st));
+                                (double *)ctx->leak_out.p, (double *)ctx->phimin.p,
+                                (double *)ctx->sums.p, (int *)ctx->minkey.p, st));
     ++ctx->launches;
     if (has_balance(ctx)) {
         const unsigned char *ot = (const unsigned char *)ctx->otab.p;
@@ -1076,7 +1080,7 @@ void rom_destroy(rom_ctx *ctx)
     invalidate_graph(ctx);
     DevBuf *bufs[] = {&ctx->sigt, &ctx->sigs, &ctx->q, &ctx->inflow_dev, &ctx->c64, &ctx->s64,
                       &ctx->z64, &ctx->w64, &ctx->c32, &ctx->s32, &ctx->w32, &ctx->items_dev,
-                      &ctx->phi, &ctx->src, &ctx->part, &ctx->partials,
+                      &ctx->phi, &ctx->src, &ctx->part, &ctx->sums, &ctx->minkey,
                       &ctx->active, &ctx->iters, &ctx->flags, &ctx->resid, &ctx->n_active,
                       &ctx->avg, &ctx->sum, &ctx->tmp, &ctx->psi, &ctx->src_ord, &ctx->Amat,
                       &ctx->dtab, &ctx->z32, &ctx->cta_begin_dev, &ctx->cta_list_dev,
@@ -1560,19 +1564,20 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     // residual chunks: combine blocks of 256 threads per sample, each thread
     // taking one or more 8-cell sectors; about 16 blocks per SM in all, so that
     // large grids stream many sectors per thread instead of paying the block's
-    // reduction per sector, and the finalize adds few partials per sample
+    // reduction per sector
     const long long max_chunks = std::max<long long>(1, (cells / 8 + 255) / 256);
     const long long want = std::max<long long>(1, (16LL * ctx->sm_count + ctx->S - 1) / ctx->S);
     const int chunks = (int)std::min(max_chunks, want);
     if (chunks != ctx->chunks) invalidate_graph(ctx);
     ctx->chunks = chunks;
     const size_t nI = (size_t)n_cells(ctx);
-    void *before[] = {ctx->phi.p,  ctx->src.p,  ctx->part.p,  ctx->partials.p, ctx->active.p,
+    void *before[] = {ctx->phi.p,  ctx->src.p,  ctx->part.p,  ctx->sums.p, ctx->minkey.p, ctx->active.p,
                       ctx->sig3.p, ctx->src3.p, ctx->acc3.p,  ctx->ss3.p,      ctx->q3.p,
                       ctx->ordsum.p, ctx->dprev.p,
                       ctx->grow.p, ctx->leak.p, ctx->bal.p, ctx->leak_out.p, ctx->phimin.p,
                       ctx->sweep_err.p, ctx->otab.p};
-    if ((rc = ensure(ctx, ctx->partials, (size_t)ctx->S * chunks * romk::kNP * sizeof(double))) ||
+    if ((rc = ensure(ctx, ctx->sums, (size_t)ctx->S * romk::kNP * sizeof(double))) ||
+        (rc = ensure(ctx, ctx->minkey, (size_t)ctx->S * sizeof(int))) ||
         (rc = ensure(ctx, ctx->active, ctx->S * sizeof(int))) ||
         (rc = ensure(ctx, ctx->iters, ctx->S * sizeof(int))) ||
         (rc = ensure(ctx, ctx->flags, ctx->S * sizeof(int))) ||
@@ -1601,7 +1606,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
         invalidate_graph(ctx);
     }
     if ((rc = ensure_state(ctx))) return rc;
-    void *after[] = {ctx->phi.p,  ctx->src.p,  ctx->part.p,  ctx->partials.p, ctx->active.p,
+    void *after[] = {ctx->phi.p,  ctx->src.p,  ctx->part.p,  ctx->sums.p, ctx->minkey.p, ctx->active.p,
                      ctx->sig3.p, ctx->src3.p, ctx->acc3.p,  ctx->ss3.p,      ctx->q3.p,
                      ctx->ordsum.p, ctx->dprev.p,
                      ctx->grow.p, ctx->leak.p, ctx->bal.p, ctx->leak_out.p, ctx->phimin.p,

@@ -8,7 +8,7 @@
 //   src    (per sample)      [S][MOM][J][NXP]   source moments for the next sweep
 //   part   (per sample)      [S][MOM][J][NXP]   moments the sweep's work items add
 //   ordinates                c, s, w [M_total] (FP32) and c, s, zeta, w (FP64)
-//   residual partials        [S][chunks][2] FP64
+//   residual and balance sums [S][kNP] FP64, smallest phi [S] (ordered-int key)
 // MOM = 1 for isotropic scattering (phi), 3 for the linear kernel (phi, Jx, Jy).
 // 3D grids keep the arrays their sweep touches in diagonal storage (Skew3 below).
 #pragma once
@@ -24,10 +24,20 @@ constexpr int kMaxG = 4;       // ordinates per sweep work item
 constexpr int kMaxWarps = 8;   // I <= 32 * 8 * 8 = 2048
 constexpr int kMaxCtaItems3 = 256;  // 3D: work items per CTA list
 
-// Partials per (sample, combine block), FP64: squared change and squared norm
-// of phi (residual), sum of sigma_T phi, sums of the three source moments of
-// the previous iterate (balance), min phi.
-constexpr int kNP = 7;
+// Per-sample sums the combine blocks add (FP64 atomics) and the finalize reads
+// and clears: squared change and squared norm of phi (residual), sum of
+// sigma_T phi, sums of the three source moments of the previous iterate
+// (balance); beside them the smallest phi of the sweep as an ordered-int key.
+constexpr int kNP = 6;
+__device__ __forceinline__ int float_order_key(float f)
+{
+    const int b = __float_as_int(f);
+    return b >= 0 ? b : b ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float float_from_order_key(int k)
+{
+    return __int_as_float(k >= 0 ? k : k ^ 0x7FFFFFFF);
+}
 
 // One sweep work item: up to kMaxG ordinates of one quadrant of one sample.
 // quad bit 0 set: c < 0 (sweep from x_R), bit 1 set: s < 0 (sweep from y_T),
@@ -74,12 +84,13 @@ struct CombineArgs {
     float *phi;
     float *src;
     const float *sigma_s, *q;
-    // balance partials (moment modes): sigma_T per cell, nullptr = sigma_t_homog
+    // balance sums (moment modes): sigma_T per cell, nullptr = sigma_t_homog
     int balance;
     const float *sigma_t;
     float sigma_t_homog;
     const int *active;
-    double *partials;           // [S][chunks][kNP]
+    double *sums;               // [S][kNP] added with FP64 atomics
+    int *minkey;                // [S] smallest phi (float_order_key), atomic min
 };
 
 // Diagonal storage of 3D cell arrays read or written by the sweep (source, sigma_T,
@@ -148,7 +159,8 @@ struct FinalizeArgs {
     int fixed_iters, max_iter;
     double tol;
     int diverge_window;         // stop a sample after this many sweeps of growing change (0: off)
-    const double *partials;     // [S][chunks][kNP]
+    double *sums;               // [S][kNP] read and cleared
+    int *minkey;                // [S] read and reset
     int *active, *iters, *flags;
     double *resid;
     double *dprev;              // [S] ||phi^k - phi^{k-1}||_2 of the previous sweep
@@ -283,7 +295,7 @@ cudaError_t launch_sweep3d(const Sweep3Args &a, int n_ctas, int nwarps, int G, i
 int sweep3d_ctas_per_sm(int nwarps, int G);
 int sweep3d_tile_cols();  // x extent of a 3D tile (8-column strips x warps per CTA)
 cudaError_t launch_combine(const CombineArgs &a, cudaStream_t st);
-// 3D: phi = the sum of the two accumulators, residual partials, and the next
+// 3D: phi = the sum of the two accumulators, residual sums, and the next
 // source sigma_S phi + q in both diagonal families; phi, sigma_S, q in family 0.
 struct Combine3Args {
     int S, chunks;
@@ -294,7 +306,8 @@ struct Combine3Args {
     float *phi;                 // [S][sk.cells] (family 0)
     const float *sigma_s, *q;   // [sk.cells] (family 0)
     const int *active;
-    double *partials;           // [S][chunks][kNP]
+    double *sums;               // [S][kNP]
+    int *minkey;                // [S]
 };
 cudaError_t launch_combine3(const Combine3Args &a, cudaStream_t st);
 cudaError_t launch_average3(const float *phi, int S, const Skew3 &sk, int I, double *avg,
@@ -310,9 +323,10 @@ cudaError_t launch_init_state(int S, int MOM, long long cells, const float *q, f
                               float *src, int *active, int *iters, int *flags, double *resid,
                               cudaStream_t st);
 // per-sample divergence and balance state of a new solve: dprev = +inf, grow = 0,
-// leak = 0, bal / leak_out / phimin = NaN
+// leak = 0, bal / leak_out / phimin = NaN, sums = 0, minkey = INT_MAX
 cudaError_t launch_init_checks(int S, double *dprev, int *grow, double *leak, double *bal,
-                               double *leak_out, double *phimin, cudaStream_t st);
+                               double *leak_out, double *phimin, double *sums, int *minkey,
+                               cudaStream_t st);
 cudaError_t launch_average(const float *phi, int S, int MOM, int I, int J, int NXP, double *avg,
                            double *sum, cudaStream_t st);
 cudaError_t launch_extract(const float *phi, int sample, int MOM, int I, int J, int NXP,

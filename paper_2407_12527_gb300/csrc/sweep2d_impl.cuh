@@ -43,21 +43,6 @@ __device__ __forceinline__ float2 neg_(float2 a) { return make_float2(-a.x, -a.y
 __device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float2 sub_(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 
-// Compensated (Kahan) FP32 sum of the boundary terms of the leakage: one term per
-// step on the boundary lanes, a few ulps of the total instead of n ulps; widened to
-// FP64 once per lane.
-struct Kahan {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v)
-    {
-        const float y = v - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
-
 // mbarrier helpers of the test hook (a bounded wait on a barrier nothing completes)
 __device__ __forceinline__ unsigned smem_u32a(const void *p)
 {
@@ -105,6 +90,22 @@ template <>
 __device__ __forceinline__ float splat<float>(float s) { return s; }
 template <>
 __device__ __forceinline__ float2 splat<float2>(float s) { return make_float2(s, s); }
+
+// Compensated (Kahan) FP32 sum of the boundary terms of the leakage, one term per
+// step (a pack of ordinates at a time): a few ulps of the total instead of n ulps;
+// widened to FP64 once per lane.
+template <class T>
+struct Kahan {
+    T s = splat<T>(0.f), c = splat<T>(0.f);
+    __device__ __forceinline__ void add(T v)
+    {
+        const T y = sub_(v, c);
+        const T t = add_(s, y);
+        c = sub_(sub_(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)hsum(s) - (double)hsum(c); }
+};
 
 template <bool DOWN>
 __device__ __forceinline__ float shfl1(float v)
@@ -398,15 +399,23 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
             setc(py[r][G == 1 ? 0 : k >> 1], G == 1 ? 0 : k & 1, v);
         }
     // net leakage of the item (moment modes): sum_l w_l (|c_l| dy sum_rows +
-    // |s_l| dx sum_cols) (psi_out - psi_in), Kahan-summed per lane
-    Kahan leak;
+    // |s_l| dx sum_cols) (psi_out - psi_in), Kahan-summed per lane.  The x-face
+    // terms use weights that are zero except on the boundary lanes, so every
+    // lane runs the same instructions (no branch in the step).
+    Kahan<T> leak;
+    T lx_out[N], lx_in[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        lx_out[p] = d == L - 1 ? o.lx[p] : splat<T>(0.f);
+        lx_in[p] = d == 0 ? o.lx[p] : splat<T>(0.f);
+    }
     if (A.leak && lane_on) {
-        float lin = 0.f;
+        T lin = splat<T>(0.f);
 #pragma unroll
         for (int r = 0; r < kCols; ++r)
 #pragma unroll
-            for (int p = 0; p < N; ++p) lin += hsum(mul_(o.ly[p], py[r][p]));
-        leak.add(-lin);
+            for (int p = 0; p < N; ++p) lin = fma_(o.ly[p], py[r][p], lin);
+        leak.add(neg_(lin));
     }
 
     T xin[kH][N];
@@ -460,14 +469,14 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
                         }
                         setc(xin[h][G == 1 ? 0 : k >> 1], G == 1 ? 0 : k & 1, v);
                     }
-                if (A.leak) {  // rows past J carry zero inflow
-                    float lin = 0.f;
+            }
+            if (A.leak && A.inflow) {  // x inflow (lane d == 0; rows past J carry zeros)
+                T lin = splat<T>(0.f);
 #pragma unroll
-                    for (int h = 0; h < kH; ++h)
+                for (int h = 0; h < kH; ++h)
 #pragma unroll
-                        for (int p = 0; p < N; ++p) lin += hsum(mul_(o.lx[p], xin[h][p]));
-                    leak.add(-lin);
-                }
+                    for (int p = 0; p < N; ++p) lin = fma_(lx_in[p], xin[h][p], lin);
+                leak.add(neg_(lin));
             }
             const bool full = full_cols && (blk + 1) * kH <= A.J;
             if (full)
@@ -476,12 +485,12 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
             else
                 sweep_block<G, MOM, SCHEME, HOMOG, XNEG, true, STORE_LATE>(
                     A, blk, yneg, col0, o, py, xin, xo, cur, out, part_i);
-            if (A.leak && d == L - 1) {  // the outflow x face; rows past J leave zeros
-                float lo = 0.f;
+            if (A.leak) {  // the outflow x face (lane d == L - 1); rows past J leave zeros
+                T lo = splat<T>(0.f);
 #pragma unroll
                 for (int h = 0; h < kH; ++h)
 #pragma unroll
-                    for (int p = 0; p < N; ++p) lo += hsum(mul_(o.lx[p], xo[h][p]));
+                    for (int p = 0; p < N; ++p) lo = fma_(lx_out[p], xo[h][p], lo);
                 leak.add(lo);
             }
         } else {
@@ -544,12 +553,12 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
     }
     if (A.leak) {  // outgoing y-edges of the lane's columns, then one FP64 add per warp
         if (lane_on) {
-            float lo = 0.f;
+            T lo = splat<T>(0.f);
 #pragma unroll
             for (int r = 0; r < kCols; ++r)
                 if (col0 + r < A.I)
 #pragma unroll
-                    for (int p = 0; p < N; ++p) lo += hsum(mul_(o.ly[p], py[r][p]));
+                    for (int p = 0; p < N; ++p) lo = fma_(o.ly[p], py[r][p], lo);
             leak.add(lo);
         }
         double lk = leak.value();
