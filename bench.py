@@ -592,95 +592,144 @@ def run_ours(args):
 
 def run_rom_vs_dom(args):
     """GPU time for ROM and for plain DOM to reach a relative l2 error of the scalar
-    flux of 1e-3 on the point-source problem.  Reference: the FP64 oracle with the
-    2D uniform set N = args.ref_n (4 N^2 ordinates), SI to 1e-9.  DOM: the uniform
-    set for growing N, one solve each (time = that solve).  ROM: M = 4 m ordinates
-    per sample, samples solved in batches, the running average compared after each
-    batch (time = cumulative GPU time of the batches)."""
+    flux of args.target (1e-3) against a fine-ordinate FP64 reference.
+
+    Reference: the FP64 oracle with the 2D Gaussian set N = args.ref_n (2 N (N + 1)
+    ordinates; N = 200: 80400), source iteration to 1e-12, cross-checked against
+    N = args.ref_check_n (its relative l2 difference is reported and must be far below
+    the target).  DOM: the uniform set N = 2 ... 32 (4 N^2 ordinates), one solve each
+    to the library tolerance (time = that solve).  ROM: M = 4 m ordinates per sample
+    for m in args.rom_m (M = 16, 36, 64), samples solved in batches, the running
+    average compared after each batch (time = cumulative GPU time of the batches);
+    for each M the first t whose running average is within the target, repeated over
+    args.rom_seeds seeds, median reported.  The bias floor of each M is the
+    least-squares fit of err(t)^2 = B^2 + V / t over the seeds' curves (the Monte
+    Carlo part falls as t^(-1/2), Sec. 4.1); ROM cannot reach a target below B.
+    Problems: the 256 x 256 point source (isotropic), Example 2.1, or the
+    Henyey-Greenstein disc (g = 0.8, sigma_S = 0.95) reduced to args.rvd_n cells per
+    side (the FP64 dense reference costs M^2 per cell and sweep)."""
     import torch
     from oracle import oracle as O
     import __graft_entry__
     __graft_entry__.build()
     from paper_2407_12527_gb300 import RomContext
 
-    p = W.point_source() if args.rvd_problem == "point_source" else W.example_2_1()
-    t0 = time.perf_counter()
-    ref_set = (O.quad_gauss_xy(args.ref_n) if args.ref_kind == "gauss"
-               else O.quad_uniform_xy(args.ref_n))
-    ref = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, [ref_set],
-                     tol=1e-9)["phi"][0]
-    ref_s = time.perf_counter() - t0
+    if args.rvd_problem == "point_source":
+        p = W.point_source()
+    elif args.rvd_problem == "example_2_1":
+        p = W.example_2_1()
+    else:
+        p = W.hg_disc(n=args.rvd_n)
+    kw = {} if p.kernel == "iso" else {"kernel": p.kernel, "g": p.g}
+
+    def reference(N):
+        t = time.perf_counter()
+        o = O.quad_gauss_xy(N) if args.ref_kind == "gauss" else O.quad_uniform_xy(N)
+        r = O.solve_xy(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q, [o], tol=1e-12,
+                       **kw)["phi"][0]
+        return r, o.M, time.perf_counter() - t
+
+    ref, ref_m, ref_s = reference(args.ref_n)
     nref = float(np.linalg.norm(ref))
 
     def rel(phi):
         return float(np.linalg.norm(phi - ref) / nref)
 
+    chk = None
+    if args.ref_check_n > 0:
+        r2, m2, s2 = reference(args.ref_check_n)
+        chk = {"N": args.ref_check_n, "M": m2, "rel_l2_to_reference": rel(r2), "host_s": s2}
+
     ctx = RomContext(0)
     ctx.set_grid(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q)
-    ctx.set_options(tol=TOL, tile_g=-1)
+    if p.kernel != "iso":
+        ctx.set_kernel(p.kernel, p.g)
+    ctx.set_options(tol=TOL, tile_g=-1, dense_precision=args.dense_precision)
     dom = []
     for N in args.dom_n:
         ctx.set_quadrature("uniform", N)
-        ctx.solve()                      # warm-up (graph capture, tuning)
-        s = ctx.solve()
-        dom.append({"N": N, "M": 4 * N * N, "ms": s["gpu_ms"], "rel_l2": rel(ctx.scalar_flux(-1))})
-    rom = []
-    for m in args.rom_m:
-        nz, nt = W.partition(m)
-        batch = args.rom_batch
-        tot_ms, acc, n = 0.0, np.zeros((p.J, p.I)), 0
-        curve = []
-        ctx.set_ordinates_seed(W.ordinate_seed(1, 7), [nz] * batch, [nt] * batch, first_sample=0)
-        ctx.solve()                      # warm-up
-        while n < args.rom_max:
-            ctx.set_ordinates_seed(W.ordinate_seed(1, 7), [nz] * batch, [nt] * batch,
-                                   first_sample=n)
-            s = ctx.solve()
-            tot_ms += s["gpu_ms"]
-            part, cnt = ctx.partial_sum()
-            acc += part
-            n += cnt
-            curve.append({"samples": n, "ms": tot_ms, "rel_l2": rel(acc / n)})
-        rom.append({"M": 4 * m, "curve": curve})
-    ctx.close()
-
+        if p.kernel == "hg":  # the tensor-core product takes at most 128 ordinates
+            ctx.set_options(tol=TOL, tile_g=-1,
+                            dense_precision=args.dense_precision if 4 * N * N <= 128 else 0)
+        ctx.solve(allow_not_converged=True)   # warm-up (graph capture, tuning)
+        s = ctx.solve(allow_not_converged=True)
+        dom.append({"N": N, "M": 4 * N * N, "ms": s["gpu_ms"], "sweeps": s["iterations_max"],
+                    "rel_l2": rel(ctx.scalar_flux(-1)),
+                    "tensor_cores": bool(p.kernel == "hg" and args.dense_precision == 1
+                                         and 4 * N * N <= 128)})
     target = args.target
 
     def first(points, tgt=target):
         hit = [q for q in points if q["rel_l2"] <= tgt]
         return hit[0] if hit else None
 
-    def rom_first(tgt):
-        hits = [(first(r["curve"], tgt), r["M"]) for r in rom]
-        hits = [(h["ms"], M, h["samples"]) for h, M in hits if h]
-        return min(hits) if hits else None
+    ctx.set_options(tol=TOL, tile_g=-1, dense_precision=args.dense_precision)
+    rom = []
+    for m in args.rom_m:
+        nz, nt = W.partition(m)
+        batch = args.rom_batch
+        runs = []
+        for rep in range(args.rom_seeds):
+            seed = W.ordinate_seed(1, 7 + rep)
+            ctx.set_ordinates_seed(seed, [nz] * batch, [nt] * batch, first_sample=0)
+            ctx.solve(allow_not_converged=True)  # warm-up
+            tot_ms, acc, n, curve = 0.0, np.zeros((p.J, p.I)), 0, []
+            while n < args.rom_max:
+                ctx.set_ordinates_seed(seed, [nz] * batch, [nt] * batch, first_sample=n)
+                s = ctx.solve(allow_not_converged=True)
+                tot_ms += s["gpu_ms"]
+                part, cnt = ctx.partial_sum()
+                acc += part
+                n += cnt
+                curve.append({"samples": n, "ms": tot_ms, "rel_l2": rel(acc / n)})
+                if curve[-1]["rel_l2"] <= target and n >= args.rom_min:
+                    break
+            runs.append({"seed": seed, "curve": curve, "at_target": first(curve)})
+        # bias floor: err(t)^2 = B^2 + V / t, least squares over every point of every run
+        ts = np.array([c["samples"] for r in runs for c in r["curve"]], dtype=np.float64)
+        e2 = np.array([c["rel_l2"] ** 2 for r in runs for c in r["curve"]])
+        A = np.stack([np.ones_like(ts), 1.0 / ts], 1)
+        (b2, v), *_ = np.linalg.lstsq(A, e2, rcond=None)
+        hits = [r["at_target"] for r in runs if r["at_target"]]
+        med = None
+        if len(hits) * 2 > len(runs):  # a median exists among the runs that reached it
+            ms_all = sorted([h["ms"] for h in hits] + [float("inf")] * (len(runs) - len(hits)))
+            sm_all = sorted([h["samples"] for h in hits] + [10 ** 9] * (len(runs) - len(hits)))
+            med = {"ms": ms_all[len(runs) // 2], "samples": sm_all[len(runs) // 2]}
+        rom.append({"M": 4 * m, "runs_reaching_target": len(hits), "runs": len(runs),
+                    "median_at_target": med,
+                    "bias_floor_rel_l2": float(np.sqrt(max(b2, 0.0))),
+                    "mc_spread_rel_l2": float(np.sqrt(max(v, 0.0))),
+                    "final": [r["curve"][-1] for r in runs]})
+    ctx.close()
 
     dom_hit = first(dom)
-    rom_hits = [(r["M"], first(r["curve"])) for r in rom]
-    rom_best = rom_first(target)
-    coarse = {}
-    for tgt in (1e-1, 3e-2, 1e-2, 3e-3):
-        d, r = first(dom, tgt), rom_first(tgt)
-        coarse[f"{tgt:g}"] = {"dom_ms": d["ms"] if d else None, "dom_M": d["M"] if d else None,
-                              "rom_ms": r[0] if r else None, "rom_M": r[1] if r else None,
-                              "rom_samples": r[2] if r else None}
+    rom_reached = [r for r in rom if r["median_at_target"]]
+    rom_best = min(rom_reached, key=lambda r: r["median_at_target"]["ms"]) if rom_reached else None
     line = {
         "metric": f"GPU time to relative l2 flux error {target:g}, ROM vs DOM ({p.name}, "
-                  f"{p.I}x{p.J})",
+                  f"{p.I}x{p.J}, kernel {p.kernel}{' g=%g' % p.g if p.kernel != 'iso' else ''})",
         "unit": "ms", "higher_is_better": False, "data": "synthetic",
-        "reference": f"FP64 oracle, 2D {args.ref_kind} set N={args.ref_n} ({ref_set.M} ordinates), "
-                     f"SI to 1e-9 ({ref_s:.0f} s on the host)",
+        "reference": f"FP64 oracle, 2D {args.ref_kind} set N={args.ref_n} ({ref_m} ordinates), "
+                     f"SI to 1e-12 ({ref_s:.0f} s on the host)",
+        "reference_check": chk,
         "dom_ms_to_target": dom_hit["ms"] if dom_hit else None,
         "dom_M_at_target": dom_hit["M"] if dom_hit else None,
-        "rom_ms_to_target": rom_best[0] if rom_best else None,
-        "rom_M_at_target": rom_best[1] if rom_best else None,
-        "rom_samples_at_target": rom_best[2] if rom_best else None,
-        "time_to_other_targets": coarse,
+        "dom_best_rel_l2": min(d["rel_l2"] for d in dom) if dom else None,
+        "rom_median_ms_to_target": rom_best["median_at_target"]["ms"] if rom_best else None,
+        "rom_M_at_target": rom_best["M"] if rom_best else None,
+        "rom_median_samples_at_target": rom_best["median_at_target"]["samples"] if rom_best else None,
         "dom": dom,
-        "rom": [{"M": r["M"], "final": r["curve"][-1],
-                 "at_target": h} for r, (_, h) in zip(rom, rom_hits)],
+        "rom": rom,
+        "settings": {"rom_batch": args.rom_batch, "rom_max": args.rom_max,
+                     "rom_seeds": args.rom_seeds, "tol": TOL,
+                     "dense_precision": args.dense_precision if p.kernel == "hg" else None},
     }
-    print(json.dumps(line))
+    out = json.dumps(line)
+    print(out)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(json.dumps(line, indent=1) + "\n")
     return 0
 
 
@@ -802,9 +851,18 @@ def main():
     ap.add_argument("--rom-vs-dom", action="store_true",
                     help="measure GPU time to a relative l2 error target, ROM vs plain DOM")
     ap.add_argument("--target", type=float, default=1e-3)
-    ap.add_argument("--ref-n", type=int, default=100)
+    ap.add_argument("--ref-n", type=int, default=200)
+    ap.add_argument("--ref-check-n", type=int, default=150,
+                    help="second reference set whose distance to the first is reported (0: none)")
+    ap.add_argument("--rom-seeds", type=int, default=5)
+    ap.add_argument("--rom-min", type=int, default=0,
+                    help="samples a ROM run always accumulates before stopping at the target")
+    ap.add_argument("--rvd-n", type=int, default=128,
+                    help="cells per side of the reduced Henyey-Greenstein disc problem")
+    ap.add_argument("--out", default="", help="also write the JSON line (indented) to this file")
     ap.add_argument("--ref-kind", default="gauss", choices=["gauss", "uniform"])
-    ap.add_argument("--rvd-problem", default="point_source", choices=["point_source", "example_2_1"])
+    ap.add_argument("--rvd-problem", default="point_source",
+                    choices=["point_source", "example_2_1", "hg_disc"])
     ap.add_argument("--dom-n", type=int, nargs="+", default=[2, 3, 4, 6, 8, 12, 16, 24, 32])
     ap.add_argument("--rom-m", type=int, nargs="+", default=[4, 9, 16],
                     help="ordinate cells per quadrant (M = 4 m)")
