@@ -184,6 +184,28 @@ int rom_set_grid_device(rom_ctx *ctx, int dim, const int64_t n[3], const double 
                         const double hi[3], const float *sigma_t, const float *sigma_s,
                         const float *q);
 
+/* Several X-Y grids in one context: the ROM samples are independent solves
+ * (Sec. 3.1 runs one discrete-ordinate problem per sample; Sec. 4.1 averages
+ * their scalar fluxes), so one batch may hold samples of different problems.
+ * Grid p has n[2p] x n[2p+1] cells on [lo[2p], hi[2p]] x [lo[2p+1], hi[2p+1]]
+ * and holds samples_per_grid[p] >= 1 consecutive samples: samples 0 ..
+ * samples_per_grid[0]-1 are on grid 0, and so on.  sigma_t, sigma_s and q are
+ * host FP64 arrays holding the grids' [J_p][I_p] blocks one after the other
+ * (same hypotheses as rom_set_grid).  The ordinate sets set afterwards (or
+ * before) must number sum_p samples_per_grid[p] samples; rom_solve checks
+ * this (ROM_ERR_STATE).  The boundaries are vacuum (the inflow setters return
+ * ROM_ERR_UNSUPPORTED) and the source iteration runs on angular moments:
+ * the isotropic or (unflagged) linear kernel without dense_source; the dense
+ * operator (Henyey-Greenstein, flagged kernels, dense_source = 1) returns
+ * ROM_ERR_UNSUPPORTED at rom_solve.  rom_get_scalar_flux(sample >= 0) returns the sample's own
+ * [J_p][I_p] grid; the average per grid comes from rom_get_grid_average
+ * (sample = -1 and rom_get_partial_sum return an error).  rom_set_grid or
+ * rom_set_grid_device returns the context to one grid.  Copies the arrays:
+ * the caller keeps ownership. */
+int rom_set_grids_xy(rom_ctx *ctx, int n_grids, const int64_t *n, const double *lo,
+                     const double *hi, const double *sigma_t, const double *sigma_s,
+                     const double *q, const int32_t *samples_per_grid);
+
 /* Isotropic inflow psi_Gamma on one face (eq. equ_1_bc): host FP64 values per
  * face cell, >= 0; NULL = vacuum.  2D: J values for the x faces, I for the y
  * faces.  3D (faces 0..5): [K][J] for the x faces, [K][I] for the y faces,
@@ -282,6 +304,10 @@ int rom_get_balance(rom_ctx *ctx, double *leakage, double *balance, double *phi_
 /* Sum over this context's samples of phi (FP64 [J][I] or [K][J][I]) and their count, for
  * combining runs over disjoint sample ranges (rom_set_ordinates_seed_offset). */
 int rom_get_partial_sum(rom_ctx *ctx, double *sum_out, int64_t *count_out);
+
+/* FP64 average over the samples of grid `grid` (Sec. 4.1) into host [J_p][I_p];
+ * with one grid, grid = 0 gives the same values as rom_get_scalar_flux(-1). */
+int rom_get_grid_average(rom_ctx *ctx, int grid, double *out);
 
 /* Library version string. */
 const char *rom_version(void);

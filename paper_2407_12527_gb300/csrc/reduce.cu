@@ -67,13 +67,25 @@ __device__ __forceinline__ void block_partials(float (&v)[6], float mn, double *
 }
 
 template <int MOM>
-__global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
+__global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A0)
 {
     const int s = blockIdx.y;
-    if (!A.active[s]) return;
+    if (!A0.active[s]) return;
+    CombineArgs A = A0;
+    long long base = (long long)s * MOM * A0.cells;  // the sample's [MOM][cells] block
+    if (A0.grids) {  // several grids: the sample's own grid and coefficient block
+        const GridDesc g = A0.grids[A0.sgrid[s]];
+        A.cells = g.cells;
+        A.I = g.I;
+        A.NXP = g.NXP;
+        A.sigma_s = A0.sigma_s + g.off;
+        A.q = A0.q + g.off;
+        if (A0.sigma_t) A.sigma_t = A0.sigma_t + g.off;
+        base = A0.soff[s];
+    }
     const long long cells = A.cells;  // a multiple of 8: every thread owns one 32-byte sector
-    float *phi = A.phi + (long long)s * MOM * cells;
-    float *src = A.src + (long long)s * MOM * cells;
+    float *phi = A.phi + base;
+    float *src = A.src + base;
     float d2f = 0.f, n2f = 0.f, mn = INFINITY, a1f = 0.f, b0f = 0.f, b1f = 0.f, b2f = 0.f;
     for (long long v = 8 * ((long long)blockIdx.x * blockDim.x + threadIdx.x); v < cells;
          v += 8LL * gridDim.x * blockDim.x) {
@@ -110,7 +122,7 @@ __global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A)
             for (int e = 0; e < 8; ++e) zero[e] = 0.f;
 #pragma unroll
             for (int m = 0; m < MOM; ++m) {
-                float *p = A.acc + ((long long)s * MOM + m) * cells + v;
+                float *p = A.acc + base + m * cells + v;
                 ld8_volatile(p, acc[m]);
                 stg8(p, zero);
             }
@@ -281,8 +293,9 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalizeArgs A)
             const double lk = A.leak[s];
             A.leak[s] = 0.0;
             const double *os = A.ordsum + 3LL * s;
-            const double rhs = A.dA * (os[0] * b0 + os[1] * b1 + os[2] * b2);
-            const double rem = A.dA * a1;
+            const double dA = A.sdA ? A.sdA[s] : A.dA;
+            const double rhs = dA * (os[0] * b0 + os[1] * b1 + os[2] * b2);
+            const double rem = dA * a1;
             const double den = fabs(lk) + fabs(rem) + fabs(rhs);
             A.bal_out[s] = den > 0.0 ? fabs(lk + rem - rhs) / den : 0.0;
             A.leak_out[s] = lk;
@@ -355,6 +368,21 @@ __global__ void init_state_kernel(int S, int MOM, long long cells, const float *
         iters[t] = 0;
         flags[t] = 0;
         resid[t] = (double)INFINITY;
+    }
+}
+
+// several grids: phi = 0 and the first source q (psi^0 = 0) for each sample on its grid
+__global__ void init_grids_kernel(int MOM, const GridDesc *grids, const int *sgrid,
+                                  const long long *soff, const float *q, float *phi, float *src)
+{
+    const int s = blockIdx.y;
+    const GridDesc g = grids[sgrid[s]];
+    const long long n = (long long)MOM * g.cells;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const long long cell = v % g.cells;
+        phi[soff[s] + v] = 0.f;
+        src[soff[s] + v] = v < g.cells ? q[g.off + cell] : 0.f;
     }
 }
 
@@ -484,6 +512,15 @@ cudaError_t launch_init_state(int S, int MOM, long long cells, const float *q, f
     int b = blocks_for(n, 256);
     if ((long long)b * 256 < S) b = (S + 255) / 256;
     init_state_kernel<<<b, 256, 0, st>>>(S, MOM, cells, q, phi, src, active, iters, flags, resid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_grids(int S, int MOM, const GridDesc *grids, const int *sgrid,
+                              const long long *soff, int max_cells, const float *q, float *phi,
+                              float *src, cudaStream_t st)
+{
+    const dim3 grid(blocks_for((long long)MOM * max_cells, 256), S);
+    init_grids_kernel<<<grid, 256, 0, st>>>(MOM, grids, sgrid, soff, q, phi, src);
     return cudaGetLastError();
 }
 

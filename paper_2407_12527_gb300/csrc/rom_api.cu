@@ -93,6 +93,18 @@ struct rom_ctx {
     int tuned_h = 0;  // rows per step of that choice
     // per-sample tables of the balance: first ordinate and count, weight sums
     DevBuf otab, ordsum;
+    // several X-Y grids in one context (rom_set_grids_xy; n_grids = 0: one grid):
+    // the first grid_samples[0] samples are on grid 0, and so on
+    int n_grids = 0;
+    std::vector<romk::GridDesc> grids;
+    std::vector<int> grid_samples;
+    std::vector<long long> avg_off;  // first value of each grid's average in avg / sum
+    long long coef_cells = 0;        // cells of the concatenated coefficient arrays
+    std::vector<int> sgrid;          // grid of each sample
+    std::vector<long long> soff;     // first float of each sample's [MOM][cells] block
+    long long state_floats = 0;      // floats of one per-sample state array (all samples)
+    long long max_cells = 0;         // largest grid's J * NXP
+    DevBuf gdesc, sgrid_dev, soff_dev, sdA_dev;
     // per-sample divergence and balance state: dprev, grow, leak (added by the
     // sweep), bal / leak_out / phimin (last sweep); the X-Y sweep's wait flag
     DevBuf dprev, grow, leak, bal, leak_out, phimin, sweep_err;
@@ -241,7 +253,24 @@ long long face_offset(const rom_ctx *ctx, int face)
 }
 
 long long n_cells(const rom_ctx *ctx) { return (long long)ctx->I * ctx->J * ctx->K; }
-long long padded_cells(const rom_ctx *ctx) { return ctx->rows * ctx->NXP; }
+// cells of the coefficient arrays: [rows][NXP], or the grids' blocks of a batch
+long long padded_cells(const rom_ctx *ctx)
+{
+    return ctx->n_grids > 0 ? ctx->coef_cells : ctx->rows * ctx->NXP;
+}
+bool batch(const rom_ctx *ctx) { return ctx->n_grids > 0; }
+// values of the sample average (all grids' averages, one after the other, in a batch)
+long long avg_cells(const rom_ctx *ctx)
+{
+    return ctx->n_grids > 0 ? ctx->avg_off[ctx->n_grids] : n_cells(ctx);
+}
+// cells of one sample's flux (its grid's, in a batch)
+long long sample_cells(const rom_ctx *ctx, int s)
+{
+    if (!batch(ctx)) return n_cells(ctx);
+    const romk::GridDesc &g = ctx->grids[ctx->sgrid[s]];
+    return (long long)g.I * g.J;
+}
 
 // prev: the context held a valid grid before this call.  A grid of the same shape
 // and extent keeps the work items, the tuned work-item size, the buffers and the
@@ -262,7 +291,9 @@ int set_grid_common(rom_ctx *ctx, bool prev, int dim, const int64_t n[3], const 
     for (int d = 0; d < dim; ++d)
         if (!(hi[d] > lo[d]) || !isfinite(lo[d]) || !isfinite(hi[d]))
             return fail(ctx, ROM_ERR_INVALID_ARG, "need hi > lo (finite)");
-    bool same = prev && ctx->dim == dim && ctx->I == (int)n[0] && ctx->J == (int)n[1] &&
+    const bool was_batch = batch(ctx);
+    ctx->n_grids = 0;  // one grid from here on
+    bool same = prev && !was_batch && ctx->dim == dim && ctx->I == (int)n[0] && ctx->J == (int)n[1] &&
                 ctx->K == (dim == 3 ? (int)n[2] : 1);
     for (int d = 0; d < 3 && same; ++d)
         same = ctx->lo[d] == (d < dim ? lo[d] : 0.0) && ctx->hi[d] == (d < dim ? hi[d] : 1.0);
@@ -447,9 +478,56 @@ int build_items3(rom_ctx *ctx)
     return ROM_OK;
 }
 
+// Batches of several grids: the grid and state offset of every sample and the
+// device tables of the grids (GridDesc), samples (grid, offset) and cell areas.
+int build_batch_tables(rom_ctx *ctx)
+{
+    long long tot = 0;
+    for (int p = 0; p < ctx->n_grids; ++p) tot += ctx->grid_samples[p];
+    if (tot != ctx->S)
+        return fail(ctx, ROM_ERR_STATE,
+                    "the grids hold %lld samples, the ordinate sets %d: set them to agree", tot,
+                    ctx->S);
+    const int MOM = ctx->MOM == 0 ? 1 : ctx->MOM;
+    ctx->sgrid.assign(ctx->S, 0);
+    ctx->soff.assign(ctx->S, 0);
+    std::vector<double> sdA(ctx->S);
+    long long off = 0;
+    int s = 0;
+    for (int p = 0; p < ctx->n_grids; ++p)
+        for (int k = 0; k < ctx->grid_samples[p]; ++k, ++s) {
+            const romk::GridDesc &g = ctx->grids[p];
+            ctx->sgrid[s] = p;
+            ctx->soff[s] = off;
+            off += (long long)MOM * g.cells;
+            sdA[s] = (double)g.dx * g.dy;
+        }
+    ctx->state_floats = off;
+    int rc;
+    if ((rc = ensure(ctx, ctx->gdesc, ctx->grids.size() * sizeof(romk::GridDesc))) ||
+        (rc = ensure(ctx, ctx->sgrid_dev, ctx->S * sizeof(int))) ||
+        (rc = ensure(ctx, ctx->soff_dev, ctx->S * sizeof(long long))) ||
+        (rc = ensure(ctx, ctx->sdA_dev, ctx->S * sizeof(double))))
+        return rc;
+    CK(cudaMemcpyAsync(ctx->gdesc.p, ctx->grids.data(), ctx->grids.size() * sizeof(romk::GridDesc),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->sgrid_dev.p, ctx->sgrid.data(), ctx->S * sizeof(int),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->soff_dev.p, ctx->soff.data(), ctx->S * sizeof(long long),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->sdA_dev.p, sdA.data(), ctx->S * sizeof(double),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // the host vectors may change before the next use
+    return ROM_OK;
+}
+
 int build_items(rom_ctx *ctx)
 {
     if (ctx->dim == 3) return build_items3(ctx);
+    if (batch(ctx)) {
+        int rc = build_batch_tables(ctx);
+        if (rc) return rc;
+    }
     const int G = choose_g(ctx);
     ctx->G_used = G;
     ctx->H_used = choose_rows(ctx);
@@ -482,6 +560,7 @@ int build_items(rom_ctx *ctx)
                 it.quad = code;
                 it.n = (int)std::min<size_t>(G, v.size() - k);
                 for (int t = 0; t < romk::kMaxG; ++t) it.ord[t] = t < it.n ? v[k + t] : v[k];
+                it.grid = batch(ctx) ? ctx->sgrid[s] : 0;
                 ctx->items.push_back(it);
             }
         }
@@ -560,6 +639,10 @@ romk::SweepArgs sweep_args(const rom_ctx *ctx)
     a.inflow_stride = ctx->inflow_stride;
     a.active = (const int *)ctx->active.p;
     a.cells = (long long)ctx->J * ctx->NXP;
+    if (batch(ctx)) {
+        a.grids = (const romk::GridDesc *)ctx->gdesc.p;
+        a.soff = (const long long *)ctx->soff_dev.p;
+    }
     a.leak = has_balance(ctx) ? (double *)ctx->leak.p : nullptr;
     a.dx = (float)((ctx->hi[0] - ctx->lo[0]) / ctx->I);
     a.dy = (float)((ctx->hi[1] - ctx->lo[1]) / ctx->J);
@@ -732,6 +815,20 @@ int prepare_dense(rom_ctx *ctx)
     return ROM_OK;
 }
 
+// One X-Y sweep launch with work items of G ordinates and H rows per step: one CTA
+// per item, as many warps as the widest grid needs.
+cudaError_t launch_xy_sweep(const rom_ctx *ctx, const romk::SweepArgs &sa, int G, int H,
+                            cudaStream_t st)
+{
+    const int L = (ctx->I + romk::kCols - 1) / romk::kCols;
+    const int nwarps = (L + 31) / 32;
+    if (batch(ctx))
+        return romk::launch_sweep2d_batch(sa, (int)ctx->items.size(), nwarps, G, ctx->opt.scheme,
+                                          ctx->MOM, H, st);
+    return romk::launch_sweep2d(sa, (int)ctx->items.size(), nwarps, G, ctx->opt.scheme,
+                                ctx->homog, ctx->MOM, H, st);
+}
+
 int launches_per_iteration(const rom_ctx *ctx)
 {
     if (ctx->dim == 3) return ctx->n_tx * ctx->n_ty + 2;
@@ -754,11 +851,7 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
                                         ctx->opt.scheme, st));
             }
     } else {
-        const romk::SweepArgs sa = sweep_args(ctx);
-        const int L = (ctx->I + romk::kCols - 1) / romk::kCols;
-        const int nwarps = (L + 31) / 32;
-        CK(romk::launch_sweep2d(sa, (int)ctx->items.size(), nwarps, ctx->G_used, ctx->opt.scheme,
-                                ctx->homog, ctx->MOM, ctx->H_used, st));
+        CK(launch_xy_sweep(ctx, sweep_args(ctx), ctx->G_used, ctx->H_used, st));
     }
     if (k1) CK(cudaEventRecord(k1, st));
     romk::CombineArgs ca{};
@@ -780,6 +873,12 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     ca.balance = has_balance(ctx) ? 1 : 0;
     ca.sigma_t = ctx->homog ? nullptr : (const float *)ctx->sigt.p;
     ca.sigma_t_homog = ctx->sigma_t_homog;
+    if (batch(ctx)) {
+        ca.grids = (const romk::GridDesc *)ctx->gdesc.p;
+        ca.sgrid = (const int *)ctx->sgrid_dev.p;
+        ca.soff = (const long long *)ctx->soff_dev.p;
+        ca.cells = ctx->max_cells;
+    }
     if (ctx->dim == 3) {
         romk::Combine3Args c3{};
         c3.S = ctx->S;
@@ -836,6 +935,7 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     fa.balance = has_balance(ctx) ? 1 : 0;
     fa.leak = (double *)ctx->leak.p;
     fa.dA = (ctx->hi[0] - ctx->lo[0]) / ctx->I * (ctx->hi[1] - ctx->lo[1]) / ctx->J;
+    fa.sdA = batch(ctx) ? (const double *)ctx->sdA_dev.p : nullptr;
     fa.ordsum = (const double *)ctx->ordsum.p;
     fa.bal_out = (double *)ctx->bal.p;
     fa.leak_out = (double *)ctx->leak_out.p;
@@ -848,6 +948,7 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
 }
 
 int ensure_state(rom_ctx *ctx);
+int init_state(rom_ctx *ctx);
 
 // tile_g = -1: time the sweep kernel of every candidate work-item size G and
 // rows per wavefront step H (2 only in the moment modes) on the current problem
@@ -855,8 +956,6 @@ int ensure_state(rom_ctx *ctx);
 int autotune_g(rom_ctx *ctx)
 {
     const int cap = source_mode(ctx) == 0 ? 2 : 4;
-    const long long cells = (long long)ctx->J * ctx->NXP;
-    const int MOMk = ctx->MOM == 0 ? 1 : ctx->MOM;
     float best_ms = 0.f;
     int best = 0, best_h = 4, rc;
     const int want_h = source_mode(ctx) == 0 ? 4 : ctx->opt.rows_per_step;  // 0: both
@@ -866,19 +965,11 @@ int autotune_g(rom_ctx *ctx)
         ctx->opt.tile_g = G;
         if ((rc = build_items(ctx))) return rc;
         if ((rc = ensure_state(ctx))) return rc;  // phi, sources, accumulators
-        CK(romk::launch_init_state(ctx->S, MOMk, cells, (const float *)ctx->q.p,
-                                   (float *)ctx->phi.p, (float *)ctx->src.p, (int *)ctx->active.p,
-                                   (int *)ctx->iters.p, (int *)ctx->flags.p,
-                                   (double *)ctx->resid.p, ctx->stream));
-        if (ctx->MOM == 0)
-            CK(romk::launch_dense_init((const float *)ctx->q.p, cells, ctx->Mtot,
-                                       (float *)ctx->src_ord.p, ctx->stream));
+        if ((rc = init_state(ctx))) return rc;
         const romk::SweepArgs sa = sweep_args(ctx);
-        const int L = (ctx->I + romk::kCols - 1) / romk::kCols;
         for (int rep = 0; rep < 4; ++rep) {
             if (rep == 1) CK(cudaEventRecord(ctx->ev0, ctx->stream));
-            CK(romk::launch_sweep2d(sa, (int)ctx->items.size(), (L + 31) / 32, G, ctx->opt.scheme,
-                                    ctx->homog, ctx->MOM, H, ctx->stream));
+            CK(launch_xy_sweep(ctx, sa, G, H, ctx->stream));
             ++ctx->launches;
         }
         CK(cudaEventRecord(ctx->ev1, ctx->stream));
@@ -917,9 +1008,11 @@ int ensure_state(rom_ctx *ctx)
             return rc;
         return ROM_OK;
     }
-    const size_t b = (size_t)padded_cells(ctx) * sizeof(float);
-    if ((rc = ensure(ctx, ctx->phi, S * MOM * b)) || (rc = ensure(ctx, ctx->src, S * MOM * b)) ||
-        (rc = ensure(ctx, ctx->part, S * MOM * b)))
+    // [S][MOM][J][NXP], or each sample's [MOM][J_p][NXP_p] block of its grid
+    const size_t b = (batch(ctx) ? (size_t)ctx->state_floats
+                                 : S * MOM * (size_t)padded_cells(ctx)) * sizeof(float);
+    if ((rc = ensure(ctx, ctx->phi, b)) || (rc = ensure(ctx, ctx->src, b)) ||
+        (rc = ensure(ctx, ctx->part, b)))
         return rc;
     return ROM_OK;
 }
@@ -954,6 +1047,16 @@ int init_state(rom_ctx *ctx)
         CK(romk::launch_init_state(ctx->S, 1, sk.cells, nullptr, (float *)ctx->phi.p, nullptr,
                                    (int *)ctx->active.p, (int *)ctx->iters.p, (int *)ctx->flags.p,
                                    (double *)ctx->resid.p, st));
+    } else if (batch(ctx)) {
+        CK(cudaMemsetAsync(ctx->part.p, 0, (size_t)ctx->state_floats * sizeof(float), st));
+        CK(romk::launch_init_state(ctx->S, MOM, 0, nullptr, nullptr, nullptr, (int *)ctx->active.p,
+                                   (int *)ctx->iters.p, (int *)ctx->flags.p,
+                                   (double *)ctx->resid.p, st));
+        CK(romk::launch_init_grids(ctx->S, MOM, (const romk::GridDesc *)ctx->gdesc.p,
+                                   (const int *)ctx->sgrid_dev.p, (const long long *)ctx->soff_dev.p,
+                                   (int)ctx->max_cells, (const float *)ctx->q.p,
+                                   (float *)ctx->phi.p, (float *)ctx->src.p, st));
+        ++ctx->launches;
     } else {
         // the sweep accumulates into part; the combine clears it
         CK(cudaMemsetAsync(ctx->part.p, 0, (size_t)ctx->S * MOM * cells * sizeof(float), st));
@@ -1088,7 +1191,8 @@ void rom_destroy(rom_ctx *ctx)
                       &ctx->acc3, &ctx->ss3, &ctx->q3, &ctx->psi_split,
                       &ctx->a_hi, &ctx->a_lo, &ctx->tc_err, &ctx->otab, &ctx->ordsum,
                       &ctx->dprev, &ctx->grow,
-                      &ctx->leak, &ctx->bal, &ctx->leak_out, &ctx->phimin, &ctx->sweep_err};
+                      &ctx->leak, &ctx->bal, &ctx->leak_out, &ctx->phimin, &ctx->sweep_err,
+                      &ctx->gdesc, &ctx->sgrid_dev, &ctx->soff_dev, &ctx->sdA_dev};
     for (DevBuf *b : bufs) release(*b);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -1226,10 +1330,120 @@ int rom_set_grid_device(rom_ctx *ctx, int dim, const int64_t n[3], const double 
     return ROM_OK;
 }
 
+int rom_set_grids_xy(rom_ctx *ctx, int n_grids, const int64_t *n, const double *lo,
+                     const double *hi, const double *sigma_t, const double *sigma_s,
+                     const double *q, const int32_t *samples_per_grid)
+{
+    if (!ctx) return ROM_ERR_INVALID_ARG;
+    if (n_grids < 1) return fail(ctx, ROM_ERR_INVALID_ARG, "n_grids must be >= 1");
+    if (!n || !lo || !hi || !sigma_t || !sigma_s || !q || !samples_per_grid)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaSetDevice(ctx->device));
+    ctx->grid_set = false;
+    std::vector<romk::GridDesc> grids(n_grids);
+    std::vector<long long> avg_off(n_grids + 1, 0), in_off(n_grids + 1, 0);
+    long long off = 0, max_cells = 0;
+    int max_i = 0, max_j = 0;
+    for (int p = 0; p < n_grids; ++p) {
+        const long long I = n[2 * p], J = n[2 * p + 1];
+        if (I < 1 || J < 1) return fail(ctx, ROM_ERR_INVALID_ARG, "grid %d: sizes must be >= 1", p);
+        if (I > 32 * romk::kMaxWarps * romk::kCols || J > (1 << 24))
+            return fail(ctx, ROM_ERR_INVALID_ARG, "grid %d: %lld x %lld is too large", p, I, J);
+        for (int d = 0; d < 2; ++d)
+            if (!(hi[2 * p + d] > lo[2 * p + d]) || !isfinite(lo[2 * p + d]) ||
+                !isfinite(hi[2 * p + d]))
+                return fail(ctx, ROM_ERR_INVALID_ARG, "grid %d: need hi > lo (finite)", p);
+        if (samples_per_grid[p] < 1)
+            return fail(ctx, ROM_ERR_INVALID_ARG, "grid %d: samples_per_grid must be >= 1", p);
+        romk::GridDesc &g = grids[p];
+        g.I = (int)I;
+        g.J = (int)J;
+        g.NXP = (int)((I + romk::kCols - 1) / romk::kCols * romk::kCols);
+        const double wx = hi[2 * p] - lo[2 * p], wy = hi[2 * p + 1] - lo[2 * p + 1];
+        g.inv_dx = (float)(I / wx);
+        g.inv_dy = (float)(J / wy);
+        g.dx = (float)(wx / I);
+        g.dy = (float)(wy / J);
+        g.off = off;
+        g.cells = J * g.NXP;
+        off += g.cells;
+        max_cells = std::max(max_cells, g.cells);
+        max_i = std::max(max_i, g.I);
+        max_j = std::max(max_j, g.J);
+        avg_off[p + 1] = avg_off[p] + I * J;
+        in_off[p + 1] = in_off[p] + I * J;
+    }
+    int rc;
+    if ((rc = ensure_host_stage(ctx, 3 * (size_t)off * sizeof(float)))) return rc;
+    float *hs = ctx->h_stage, *hss = hs + off, *hq = hss + off;
+    for (int p = 0; p < n_grids; ++p) {
+        const romk::GridDesc &g = grids[p];
+        for (long long j = 0; j < g.J; ++j) {
+            const long long src = in_off[p] + j * g.I, dst = g.off + j * g.NXP;
+            for (int i = 0; i < g.I; ++i) {
+                const double x = sigma_t[src + i], y = sigma_s[src + i], z = q[src + i];
+                if (!(isfinite(x) && isfinite(y) && isfinite(z) && y >= 0.0 && y < x && z >= 0.0))
+                    return fail(ctx, ROM_ERR_INVALID_ARG,
+                                "grid %d, cell %lld: need 0 <= sigma_S < sigma_T and q >= 0 "
+                                "(got %g, %g, %g)", p, j * g.I + i, x, y, z);
+                hs[dst + i] = (float)x;
+                hss[dst + i] = (float)y;
+                hq[dst + i] = (float)z;
+            }
+            for (int i = g.I; i < g.NXP; ++i) {
+                hs[dst + i] = 1.f;
+                hss[dst + i] = 0.f;
+                hq[dst + i] = 0.f;
+            }
+        }
+    }
+    // the context's own grid fields hold the largest extents (the sweep's block
+    // width); the per-grid sizes travel in the grid table
+    ctx->n_grids = 0;
+    ctx->dim = 2;
+    ctx->I = max_i;
+    ctx->J = max_j;
+    ctx->K = 1;
+    ctx->rows = max_j;
+    ctx->NXP = (max_i + romk::kCols - 1) / romk::kCols * romk::kCols;
+    for (int d = 0; d < 3; ++d) {
+        ctx->lo[d] = d < 2 ? lo[d] : 0.0;
+        ctx->hi[d] = d < 2 ? hi[d] : 1.0;
+    }
+    for (int f = 0; f < 6; ++f) {
+        ctx->inflow_iso[f].clear();
+        ctx->inflow_ord[f].clear();
+    }
+    ctx->grids = grids;
+    ctx->grid_samples.assign(samples_per_grid, samples_per_grid + n_grids);
+    ctx->avg_off = avg_off;
+    ctx->coef_cells = off;
+    ctx->max_cells = max_cells;
+    ctx->n_grids = n_grids;
+    ctx->solved = false;
+    ctx->inflow_dirty = true;
+    ctx->items_dirty = true;
+    ctx->tuned_g = 0;
+    ctx->tuned_h = 0;
+    invalidate_graph(ctx);
+    set_homog(ctx, false, 1.f);  // sigma_T is read per cell (the grids' blocks)
+    const size_t bytes = (size_t)off * sizeof(float);
+    if ((rc = ensure(ctx, ctx->sigt, bytes)) || (rc = ensure(ctx, ctx->sigs, bytes)) ||
+        (rc = ensure(ctx, ctx->q, bytes)))
+        return rc;
+    CK(cudaMemcpyAsync(ctx->sigt.p, hs, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->sigs.p, hss, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->q.p, hq, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->grid_set = true;
+    return ROM_OK;
+}
+
 int rom_set_inflow_isotropic(rom_ctx *ctx, int face, const double *psi_face)
 {
     if (!ctx) return ROM_ERR_INVALID_ARG;
     if (!ctx->grid_set) return fail(ctx, ROM_ERR_STATE, "set the grid first");
+    if (batch(ctx)) return fail(ctx, ROM_ERR_UNSUPPORTED, "several grids: vacuum boundaries only");
     if (face < 0 || face >= n_faces(ctx))
         return fail(ctx, ROM_ERR_INVALID_ARG, "face must be 0..%d", n_faces(ctx) - 1);
     ctx->inflow_iso[face].clear();
@@ -1251,6 +1465,7 @@ int rom_set_inflow_ordinates(rom_ctx *ctx, int face, const double *psi)
     if (!ctx) return ROM_ERR_INVALID_ARG;
     if (!ctx->grid_set) return fail(ctx, ROM_ERR_STATE, "set the grid first");
     if (ctx->ord_source == ORD_NONE) return fail(ctx, ROM_ERR_STATE, "set the ordinates first");
+    if (batch(ctx)) return fail(ctx, ROM_ERR_UNSUPPORTED, "several grids: vacuum boundaries only");
     if (face < 0 || face >= n_faces(ctx))
         return fail(ctx, ROM_ERR_INVALID_ARG, "face must be 0..%d", n_faces(ctx) - 1);
     ctx->inflow_iso[face].clear();
@@ -1542,9 +1757,12 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     if (ctx->ord_source == ORD_NONE) return fail(ctx, ROM_ERR_STATE, "set the ordinates first");
     CK(cudaSetDevice(ctx->device));
     int rc;
-    const long long cells = padded_cells(ctx);
+    const long long cells = batch(ctx) ? ctx->max_cells : padded_cells(ctx);
     const int mode = source_mode(ctx);
     const int MOM = mode == 0 ? 1 : mode;  // moments kept per sample
+    if (batch(ctx) && mode == 0)
+        return fail(ctx, ROM_ERR_UNSUPPORTED,
+                    "several grids support the moment modes only (isotropic or linear kernel)");
     if (ctx->dim == 3 && mode != 1)
         return fail(ctx, ROM_ERR_UNSUPPORTED,
                     "3D grids support the isotropic kernel with angular moments only");
@@ -1570,7 +1788,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
     const int chunks = (int)std::min(max_chunks, want);
     if (chunks != ctx->chunks) invalidate_graph(ctx);
     ctx->chunks = chunks;
-    const size_t nI = (size_t)n_cells(ctx);
+    const size_t nI = (size_t)avg_cells(ctx);
     void *before[] = {ctx->phi.p,  ctx->src.p,  ctx->part.p,  ctx->sums.p, ctx->minkey.p, ctx->active.p,
                       ctx->sig3.p, ctx->src3.p, ctx->acc3.p,  ctx->ss3.p,      ctx->q3.p,
                       ctx->ordsum.p, ctx->dprev.p,
@@ -1668,7 +1886,18 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
         CK(romk::launch_average3((const float *)ctx->phi.p, ctx->S,
                                  romk::make_skew3(ctx->J, ctx->K, ctx->NXP), ctx->I,
                                  (double *)ctx->avg.p, (double *)ctx->sum.p, ctx->stream));
-    else
+    else if (batch(ctx)) {  // each grid's samples are consecutive [MOM][J_p][NXP_p] blocks
+        int s0 = 0;
+        for (int p = 0; p < ctx->n_grids; ++p) {
+            const romk::GridDesc &g = ctx->grids[p];
+            CK(romk::launch_average((const float *)ctx->phi.p + ctx->soff[s0],
+                                    ctx->grid_samples[p], MOM, g.I, g.J, g.NXP,
+                                    (double *)ctx->avg.p + ctx->avg_off[p],
+                                    (double *)ctx->sum.p + ctx->avg_off[p], ctx->stream));
+            s0 += ctx->grid_samples[p];
+        }
+        ctx->launches += ctx->n_grids - 1;
+    } else
         CK(romk::launch_average((const float *)ctx->phi.p, ctx->S, MOM, ctx->I, (int)ctx->rows,
                                 ctx->NXP, (double *)ctx->avg.p, (double *)ctx->sum.p,
                                 ctx->stream));
@@ -1725,7 +1954,7 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
         const int it = ctx->h_iters[s];
         st.iterations_max = std::max(st.iterations_max, it);
         st.iterations_min = std::min(st.iterations_min, it);
-        st.updates += (int64_t)n_cells(ctx) * ctx->M[s] * it;
+        st.updates += (int64_t)sample_cells(ctx, s) * ctx->M[s] * it;
         const double r = ctx->h_resid[s];
         if (!(r <= st.residual_max)) st.residual_max = r;
         if (has_balance(ctx) && !(ctx->h_bal[s] <= st.balance_max)) st.balance_max = ctx->h_bal[s];
@@ -1761,6 +1990,12 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
 // phi of one sample -> out[n_cells] (device), from the layout its dimension keeps
 cudaError_t extract_phi(rom_ctx *ctx, int sample, double *out)
 {
+    if (batch(ctx)) {
+        const romk::GridDesc &g = ctx->grids[ctx->sgrid[sample]];
+        return romk::launch_extract((const float *)ctx->phi.p + ctx->soff[sample], 0,
+                                    ctx->MOM == 0 ? 1 : ctx->MOM, g.I, g.J, g.NXP, out,
+                                    ctx->stream);
+    }
     if (ctx->dim == 3)
         return romk::launch_extract3((const float *)ctx->phi.p, sample,
                                      romk::make_skew3(ctx->J, ctx->K, ctx->NXP), ctx->I, out,
@@ -1774,8 +2009,11 @@ int rom_get_scalar_flux(rom_ctx *ctx, int sample, double *out)
     if (!ctx || !out) return fail(ctx, ROM_ERR_INVALID_ARG, "NULL argument");
     if (!ctx->solved) return fail(ctx, ROM_ERR_STATE, "call rom_solve first");
     if (sample < -1 || sample >= ctx->S) return fail(ctx, ROM_ERR_INVALID_ARG, "bad sample %d", sample);
+    if (sample == -1 && batch(ctx))
+        return fail(ctx, ROM_ERR_INVALID_ARG,
+                    "several grids: read each grid's average with rom_get_grid_average");
     CK(cudaSetDevice(ctx->device));
-    const size_t nI = (size_t)n_cells(ctx);
+    const size_t nI = (size_t)(sample >= 0 ? sample_cells(ctx, sample) : n_cells(ctx));
     if (sample >= 0) {
         int rc = ensure(ctx, ctx->tmp, nI * sizeof(double));
         if (rc) return rc;
@@ -1796,8 +2034,11 @@ int rom_get_scalar_flux_device(rom_ctx *ctx, int sample, double *out)
     if (!ctx || !out) return fail(ctx, ROM_ERR_INVALID_ARG, "NULL argument");
     if (!ctx->solved) return fail(ctx, ROM_ERR_STATE, "call rom_solve first");
     if (sample < -1 || sample >= ctx->S) return fail(ctx, ROM_ERR_INVALID_ARG, "bad sample %d", sample);
+    if (sample == -1 && batch(ctx))
+        return fail(ctx, ROM_ERR_INVALID_ARG,
+                    "several grids: read each grid's average with rom_get_grid_average");
     CK(cudaSetDevice(ctx->device));
-    const size_t nI = (size_t)n_cells(ctx);
+    const size_t nI = (size_t)(sample >= 0 ? sample_cells(ctx, sample) : n_cells(ctx));
     if (sample >= 0) {
         CK(extract_phi(ctx, sample, out));
         ++ctx->launches;
@@ -1832,10 +2073,28 @@ int rom_get_balance(rom_ctx *ctx, double *leakage, double *balance, double *phi_
     return ROM_OK;
 }
 
+int rom_get_grid_average(rom_ctx *ctx, int grid, double *out)
+{
+    if (!ctx || !out) return fail(ctx, ROM_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->solved) return fail(ctx, ROM_ERR_STATE, "call rom_solve first");
+    const int n = batch(ctx) ? ctx->n_grids : 1;
+    if (grid < 0 || grid >= n) return fail(ctx, ROM_ERR_INVALID_ARG, "bad grid %d", grid);
+    CK(cudaSetDevice(ctx->device));
+    const long long o = batch(ctx) ? ctx->avg_off[grid] : 0;
+    const long long len = batch(ctx) ? ctx->avg_off[grid + 1] - o : n_cells(ctx);
+    CK(cudaMemcpyAsync(out, (const double *)ctx->avg.p + o, (size_t)len * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ROM_OK;
+}
+
 int rom_get_partial_sum(rom_ctx *ctx, double *sum_out, int64_t *count_out)
 {
     if (!ctx) return ROM_ERR_INVALID_ARG;
     if (!ctx->solved) return fail(ctx, ROM_ERR_STATE, "call rom_solve first");
+    if (batch(ctx))
+        return fail(ctx, ROM_ERR_UNSUPPORTED,
+                    "several grids: the partial sums are per grid (rom_get_grid_average)");
     CK(cudaSetDevice(ctx->device));
     if (sum_out) {
         CK(cudaMemcpyAsync(sum_out, ctx->sum.p, (size_t)n_cells(ctx) * sizeof(double),

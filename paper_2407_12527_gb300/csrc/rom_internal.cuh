@@ -47,6 +47,17 @@ struct SweepItem {
     int quad;
     int n;
     int ord[kMaxG];
+    int grid;  // batches of several X-Y grids: the sample's grid (else 0)
+};
+
+// One grid of a batch of several X-Y grids (rom_set_grids_xy): its sizes and
+// cell widths, and where its [J][NXP] cell arrays start in the concatenated
+// coefficient arrays.
+struct GridDesc {
+    int I, J, NXP;
+    float inv_dx, inv_dy, dx, dy;
+    long long off;    // first cell of the grid's coefficient arrays
+    long long cells;  // J * NXP
 };
 
 struct SweepArgs {
@@ -65,6 +76,10 @@ struct SweepArgs {
     long long inflow_stride;    // per ordinate (0 = same values for every ordinate)
     const int *active;          // [S] samples still iterating
     long long cells;            // J * NXP
+    // several grids (nullptr: the one grid above): each item takes its grid's
+    // sizes and coefficient block, and its sample's state starts at soff[sample]
+    const GridDesc *grids;      // [grids]
+    const long long *soff;      // [S] first float of the sample's [MOM][cells] block
     // moment modes: the net leakage of each sample's sweep (nullptr: not kept)
     double *leak;               // [S]
     float dx, dy;               // leakage weights |c| dy, |s| dx
@@ -88,6 +103,10 @@ struct CombineArgs {
     int balance;
     const float *sigma_t;
     float sigma_t_homog;
+    // several grids (nullptr: one): the sample's grid and state offset
+    const GridDesc *grids;
+    const int *sgrid;           // [S]
+    const long long *soff;      // [S]
     const int *active;
     double *sums;               // [S][kNP] added with FP64 atomics
     int *minkey;                // [S] smallest phi (float_order_key), atomic min
@@ -171,6 +190,7 @@ struct FinalizeArgs {
     int balance;
     double *leak;
     double dA;
+    const double *sdA;          // [S] cell area per sample (several grids), else nullptr
     const double *ordsum;
     double *bal_out, *leak_out, *phimin_out;  // [S] values of each sample's last sweep
     int *n_active;
@@ -290,6 +310,9 @@ cudaError_t launch_sweep2d(const SweepArgs &a, int n_items, int nwarps, int G, i
                            bool homog, int mom, int rows, cudaStream_t st);
 cudaError_t launch_sweep2d_rows2(const SweepArgs &a, int n_items, int nwarps, int G, int scheme,
                                  bool homog, int mom, cudaStream_t st);
+// batches of several grids (a.grids, a.soff set): mom 1 or 3, rows 2 or 4
+cudaError_t launch_sweep2d_batch(const SweepArgs &a, int n_items, int nwarps, int G, int scheme,
+                                 int mom, int rows, cudaStream_t st);
 cudaError_t launch_sweep3d(const Sweep3Args &a, int n_ctas, int nwarps, int G, int scheme,
                            cudaStream_t st);
 int sweep3d_ctas_per_sm(int nwarps, int G);
@@ -329,6 +352,10 @@ cudaError_t launch_init_checks(int S, double *dprev, int *grow, double *leak, do
                                cudaStream_t st);
 cudaError_t launch_average(const float *phi, int S, int MOM, int I, int J, int NXP, double *avg,
                            double *sum, cudaStream_t st);
+// several grids: phi = 0 and the first source q for every sample on its own grid
+cudaError_t launch_init_grids(int S, int MOM, const GridDesc *grids, const int *sgrid,
+                              const long long *soff, int max_cells, const float *q, float *phi,
+                              float *src, cudaStream_t st);
 cudaError_t launch_extract(const float *phi, int sample, int MOM, int I, int J, int NXP,
                            double *out, cudaStream_t st);
 cudaError_t launch_pad_grid(const float *st_in, const float *ss_in, const float *q_in, int I,

@@ -10,6 +10,9 @@
 #ifndef SWEEP2D_WITH_DENSE
 #define SWEEP2D_WITH_DENSE 0
 #endif
+#ifndef SWEEP2D_BATCH
+#define SWEEP2D_BATCH 0  // 1: the kernels of batches of several grids (SweepArgs::grids)
+#endif
 #include <cuda_bf16.h>
 
 #include "rom_internal.cuh"
@@ -430,9 +433,12 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
 #pragma unroll
     for (int m = 0; m < NS; ++m)
         srcp[m] = MOM == 0 ? A.src + (long long)o.ord[m] * A.cells
-                           : A.src + ((long long)it.sample * MOM + m) * A.cells;
+                           : A.src + (A.soff ? A.soff[it.sample]
+                                             : (long long)it.sample * MOM * A.cells) +
+                                 m * A.cells;
     // moments: the sample's accumulator [n_out][cells]
-    float *part_i = A.part + (long long)it.sample * n_out(MOM) * A.cells;
+    float *part_i = A.part + (A.soff ? A.soff[it.sample]
+                                     : (long long)it.sample * n_out(MOM) * A.cells);
 
     // The rows of the lane's block for step t + PD are loaded at the start of
     // step t into a ring of PD + 1 register buffers indexed by t (the same index
@@ -568,11 +574,24 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &A, const SweepItem &
     }
 }
 
-template <int G, int MOM, int SCHEME, bool HOMOG>
-__global__ void __launch_bounds__(32 * kMaxWarps) sweep2d_kernel(const SweepArgs A)
+template <int G, int MOM, int SCHEME, bool HOMOG, bool BATCH>
+__global__ void __launch_bounds__(32 * kMaxWarps) sweep2d_kernel(const SweepArgs A0)
 {
-    const SweepItem it = A.items[blockIdx.x];
-    if (!A.active[it.sample]) return;
+    const SweepItem it = A0.items[blockIdx.x];
+    if (!A0.active[it.sample]) return;
+    SweepArgs A = A0;
+    if constexpr (BATCH) {  // the item's own grid
+        const GridDesc g = A0.grids[it.grid];
+        A.I = g.I;
+        A.J = g.J;
+        A.NXP = g.NXP;
+        A.inv_dx = g.inv_dx;
+        A.inv_dy = g.inv_dy;
+        A.dx = g.dx;
+        A.dy = g.dy;
+        A.sigma_t = A0.sigma_t + g.off;
+        A.cells = g.cells;
+    }
     if (A.stall) {  // test hook: every warp waits on a barrier that nothing completes
         __shared__ unsigned long long never;
         if (threadIdx.x == 0)
@@ -630,13 +649,20 @@ cudaError_t launch_g(const SweepArgs &a, int n_items, int nwarps, int scheme, bo
                      cudaStream_t st)
 {
     const dim3 grid(n_items), block(32 * nwarps);
+#if SWEEP2D_BATCH
+    // several grids: sigma_T read per cell (the grids' coefficient blocks)
+    (void)homog;
+    if (scheme == 0) sweep2d_kernel<G, MOM, 0, false, true><<<grid, block, 0, st>>>(a);
+    else sweep2d_kernel<G, MOM, 1, false, true><<<grid, block, 0, st>>>(a);
+#else
     if (scheme == 0) {
-        if (homog) sweep2d_kernel<G, MOM, 0, true><<<grid, block, 0, st>>>(a);
-        else sweep2d_kernel<G, MOM, 0, false><<<grid, block, 0, st>>>(a);
+        if (homog) sweep2d_kernel<G, MOM, 0, true, false><<<grid, block, 0, st>>>(a);
+        else sweep2d_kernel<G, MOM, 0, false, false><<<grid, block, 0, st>>>(a);
     } else {
-        if (homog) sweep2d_kernel<G, MOM, 1, true><<<grid, block, 0, st>>>(a);
-        else sweep2d_kernel<G, MOM, 1, false><<<grid, block, 0, st>>>(a);
+        if (homog) sweep2d_kernel<G, MOM, 1, true, false><<<grid, block, 0, st>>>(a);
+        else sweep2d_kernel<G, MOM, 1, false, false><<<grid, block, 0, st>>>(a);
     }
+#endif
     return cudaGetLastError();
 }
 

@@ -78,6 +78,7 @@ SIGNATURES = {
     "rom_set_options": (_i, [_vp, ctypes.POINTER(rom_options)]),
     "rom_set_grid": (_i, [_vp, _i, _i64p, _dp, _dp, _dp, _dp, _dp]),
     "rom_set_grid_device": (_i, [_vp, _i, _i64p, _dp, _dp, _vp, _vp, _vp]),
+    "rom_set_grids_xy": (_i, [_vp, _i, _i64p, _dp, _dp, _dp, _dp, _dp, _i32p]),
     "rom_set_inflow_isotropic": (_i, [_vp, _i, _dp]),
     "rom_set_inflow_ordinates": (_i, [_vp, _i, _dp]),
     "rom_set_ordinates": (_i, [_vp, _i, _i32p, _dp, _dp]),
@@ -94,6 +95,7 @@ SIGNATURES = {
     "rom_get_iterations": (_i, [_vp, _i32p, _dp]),
     "rom_get_partial_sum": (_i, [_vp, _dp, _i64p]),
     "rom_get_balance": (_i, [_vp, _dp, _dp, _dp]),
+    "rom_get_grid_average": (_i, [_vp, _i, _dp]),
     "rom_sweep_xy_noalloc": (_i, [_vp, _i, _i, ctypes.c_double, ctypes.c_double, _i, _vp, _i,
                                   _i32p, _dp, _dp, _vp, _vp, ctypes.c_char_p, ctypes.c_size_t]),
 }
@@ -158,6 +160,7 @@ class RomContext:
         self.K = 1
         self.dim = 2
         self.n_samples = 0
+        self.grid_shapes = None  # [(J_p, I_p)] of a batch of several grids
 
     def close(self):
         if self.h:
@@ -198,6 +201,36 @@ class RomContext:
         self._check(self.L.rom_set_grid(self.h, 2, _ptr(n, _i64p), _ptr(lo), _ptr(hi), _ptr(st),
                                         _ptr(ss), _ptr(qq)), "rom_set_grid")
         self.I, self.J, self.K, self.dim = I, J, 1, 2
+        self.grid_shapes = None
+
+    def set_grids(self, grids, samples_per_grid):
+        """Several X-Y grids in one batch: grids = [(I, J, bounds, sigma_t, sigma_s, q), ...],
+        grid p holding samples_per_grid[p] consecutive samples."""
+        n = np.array([[g[0], g[1]] for g in grids], dtype=np.int64).reshape(-1)
+        lo = _f64(np.array([[g[2][0], g[2][2]] for g in grids]).reshape(-1))
+        hi = _f64(np.array([[g[2][1], g[2][3]] for g in grids]).reshape(-1))
+        st, ss, qq = (_f64(np.concatenate([np.broadcast_to(g[k], (g[1], g[0])).reshape(-1)
+                                           for g in grids])) for k in (3, 4, 5))
+        spg = np.ascontiguousarray(np.asarray(samples_per_grid, dtype=np.int32))
+        self._check(self.L.rom_set_grids_xy(self.h, len(grids), _ptr(n, _i64p), _ptr(lo), _ptr(hi),
+                                            _ptr(st), _ptr(ss), _ptr(qq), _ptr(spg, _i32p)),
+                    "rom_set_grids_xy")
+        self.grid_shapes = [(int(g[1]), int(g[0])) for g in grids]
+        self.sample_grid = np.repeat(np.arange(len(grids)), spg)
+        self.I = max(g[0] for g in grids)
+        self.J = max(g[1] for g in grids)
+        self.K, self.dim = 1, 2
+
+    def grid_average(self, grid) -> np.ndarray:
+        """FP64 sample average of the samples on grid `grid`, [J_p, I_p]."""
+        if self.grid_shapes:
+            ok = 0 <= grid < len(self.grid_shapes)
+            shape = self.grid_shapes[grid] if ok else (1,)  # the library rejects a bad index
+        else:
+            shape = self._shape()
+        out = np.zeros(shape)
+        self._check(self.L.rom_get_grid_average(self.h, grid, _ptr(out)), "rom_get_grid_average")
+        return out
 
     def set_grid3(self, I, J, K, bounds, sigma_t, sigma_s, q):
         """3D grid: bounds = (x_L, x_R, y_B, y_T, z_B, z_T); arrays [K, J, I]."""
@@ -208,6 +241,7 @@ class RomContext:
         self._check(self.L.rom_set_grid(self.h, 3, _ptr(n, _i64p), _ptr(lo), _ptr(hi), _ptr(st),
                                         _ptr(ss), _ptr(qq)), "rom_set_grid")
         self.I, self.J, self.K, self.dim = I, J, K, 3
+        self.grid_shapes = None
 
     def set_grid3_device(self, I, J, K, bounds, sigma_t, sigma_s, q):
         """sigma_t, sigma_s, q: contiguous float32 CUDA tensors [K, J, I] (torch)."""
@@ -221,6 +255,7 @@ class RomContext:
                                                _vp(sigma_t.data_ptr()), _vp(sigma_s.data_ptr()),
                                                _vp(q.data_ptr())), "rom_set_grid_device")
         self.I, self.J, self.K, self.dim = I, J, K, 3
+        self.grid_shapes = None
 
     def set_grid_device(self, I, J, bounds, sigma_t, sigma_s, q):
         """sigma_t, sigma_s, q: contiguous float32 CUDA tensors [J, I] (torch)."""
@@ -234,6 +269,7 @@ class RomContext:
                                                _vp(sigma_t.data_ptr()), _vp(sigma_s.data_ptr()),
                                                _vp(q.data_ptr())), "rom_set_grid_device")
         self.I, self.J, self.K, self.dim = I, J, 1, 2
+        self.grid_shapes = None
 
     def set_inflow_isotropic(self, face, values):
         f = FACES[face] if isinstance(face, str) else face
@@ -301,7 +337,8 @@ class RomContext:
         return (self.K, self.J, self.I) if self.dim == 3 else (self.J, self.I)
 
     def scalar_flux(self, sample=-1) -> np.ndarray:
-        out = np.zeros(self._shape())
+        out = np.zeros(self.grid_shapes[self.sample_grid[sample]]
+                       if self.grid_shapes and sample >= 0 else self._shape())
         self._check(self.L.rom_get_scalar_flux(self.h, sample, _ptr(out)), "rom_get_scalar_flux")
         return out
 
