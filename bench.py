@@ -607,12 +607,18 @@ def run_rom_vs_dom(args):
     Carlo part falls as t^(-1/2), Sec. 4.1); ROM cannot reach a target below B.
     Problems: the 256 x 256 point source (isotropic), Example 2.1, or the
     Henyey-Greenstein disc (g = 0.8, sigma_S = 0.95) reduced to args.rvd_n cells per
-    side (the FP64 dense reference costs M^2 per cell and sweep)."""
+    side (the FP64 dense reference costs M^2 per cell and sweep).  The disc runs with
+    row-normalised kernel matrices on both sides (the normalisation the Remark of
+    Sec. 3.1 offers for sigma_S / sigma_T near 1): unnormalised, a 16-ordinate set
+    puts w P(u, u) = (1 + g) / (1 - g)^2 / 16 = 2.8 on the diagonal alone, the
+    source iteration's spectral radius exceeds 1 and the solve diverges.  A ROM run
+    stops at args.rom_max samples or after args.rom_max_ms of GPU time."""
     import torch
     from oracle import oracle as O
     import __graft_entry__
     __graft_entry__.build()
     from paper_2407_12527_gb300 import RomContext
+    from paper_2407_12527_gb300.rom import KERNEL_FLAG_NORMALIZE
 
     if args.rvd_problem == "point_source":
         p = W.point_source()
@@ -621,6 +627,9 @@ def run_rom_vs_dom(args):
     else:
         p = W.hg_disc(n=args.rvd_n)
     kw = {} if p.kernel == "iso" else {"kernel": p.kernel, "g": p.g}
+    norm = p.kernel == "hg"
+    if norm:
+        kw["normalize_rows"] = True
 
     def reference(N):
         t = time.perf_counter()
@@ -643,7 +652,7 @@ def run_rom_vs_dom(args):
     ctx = RomContext(0)
     ctx.set_grid(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q)
     if p.kernel != "iso":
-        ctx.set_kernel(p.kernel, p.g)
+        ctx.set_kernel(p.kernel, p.g, KERNEL_FLAG_NORMALIZE if norm else 0)
     ctx.set_options(tol=TOL, tile_g=-1, dense_precision=args.dense_precision)
     dom = []
     for N in args.dom_n:
@@ -674,7 +683,7 @@ def run_rom_vs_dom(args):
             ctx.set_ordinates_seed(seed, [nz] * batch, [nt] * batch, first_sample=0)
             ctx.solve(allow_not_converged=True)  # warm-up
             tot_ms, acc, n, curve = 0.0, np.zeros((p.J, p.I)), 0, []
-            while n < args.rom_max:
+            while n < args.rom_max and tot_ms < args.rom_max_ms:
                 ctx.set_ordinates_seed(seed, [nz] * batch, [nt] * batch, first_sample=n)
                 s = ctx.solve(allow_not_converged=True)
                 tot_ms += s["gpu_ms"]
@@ -708,7 +717,8 @@ def run_rom_vs_dom(args):
     rom_best = min(rom_reached, key=lambda r: r["median_at_target"]["ms"]) if rom_reached else None
     line = {
         "metric": f"GPU time to relative l2 flux error {target:g}, ROM vs DOM ({p.name}, "
-                  f"{p.I}x{p.J}, kernel {p.kernel}{' g=%g' % p.g if p.kernel != 'iso' else ''})",
+                  f"{p.I}x{p.J}, kernel {p.kernel}{' g=%g' % p.g if p.kernel != 'iso' else ''}"
+                  f"{', rows normalised' if norm else ''})",
         "unit": "ms", "higher_is_better": False, "data": "synthetic",
         "reference": f"FP64 oracle, 2D {args.ref_kind} set N={args.ref_n} ({ref_m} ordinates), "
                      f"SI to 1e-12 ({ref_s:.0f} s on the host)",
@@ -722,6 +732,7 @@ def run_rom_vs_dom(args):
         "dom": dom,
         "rom": rom,
         "settings": {"rom_batch": args.rom_batch, "rom_max": args.rom_max,
+                     "rom_max_ms": args.rom_max_ms,
                      "rom_seeds": args.rom_seeds, "tol": TOL,
                      "dense_precision": args.dense_precision if p.kernel == "hg" else None},
     }
@@ -867,6 +878,8 @@ def main():
     ap.add_argument("--rom-m", type=int, nargs="+", default=[4, 9, 16],
                     help="ordinate cells per quadrant (M = 4 m)")
     ap.add_argument("--rom-batch", type=int, default=256)
+    ap.add_argument("--rom-max-ms", type=float, default=30000.0,
+                    help="GPU time after which one ROM run stops accumulating samples")
     ap.add_argument("--rom-max", type=int, default=4096)
     ap.add_argument("--paper-tables", action="store_true",
                     help="Example 2.1 ROM error / bias table and ray-effect measure (Sec. 4.2)")
