@@ -838,7 +838,7 @@ def main():
     ap.add_argument("--check-every", type=int, default=0,
                     help="0: device-side source-iteration loop (CUDA graph); k > 0: host loop "
                          "checking every k sweeps (profilers cannot look inside the graph loop)")
-    ap.add_argument("--rows-per-step", type=int, default=0, choices=[0, 2, 4],
+    ap.add_argument("--rows-per-step", type=int, default=0, choices=[0, 1, 2, 4],
                     help="X-Y sweep rows per wavefront step (0: 4, or measured with --tile-g -1); "
                          "fixing it (with --tile-g) reproduces the autotuned shape in profiler "
                          "captures")

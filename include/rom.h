@@ -105,9 +105,11 @@ typedef struct rom_options {
                      /* 128 ordinates per sample and 2048 samples per context, else        */
                      /* ROM_ERR_UNSUPPORTED)                                               */
     int rows_per_step; /* X-Y sweep: grid rows a lane advances per wavefront step; 0 = 4,  */
-                     /* or the measured choice with tile_g = -1 (2 or 4); 2 or 4 forces it  */
-                     /* (2 only in the isotropic and linear-kernel moment modes, the dense */
-                     /* operator mode runs 4); other values are ROM_ERR_INVALID_ARG        */
+                     /* or the measured choice with tile_g = -1 (1, 2 or 4); 1, 2 or 4     */
+                     /* forces it (1 and 2 only in the isotropic and linear-kernel moment  */
+                     /* modes, the dense operator mode runs 4; 1 solves each lane's 8-cell */
+                     /* upwind recurrence as a prefix of affine maps); other values are    */
+                     /* ROM_ERR_INVALID_ARG                                                */
     int diverge_window; /* 16: a sample whose change ||phi^k - phi^{k-1}||_2 grew in this  */
                      /* many consecutive sweeps (while above tol) stops as diverged         */
                      /* (ROM_ERR_DIVERGED); 0 turns the test off                            */
@@ -136,8 +138,8 @@ typedef struct rom_stats {
     int64_t source_launches; /* contractions timed (dense operator only)                  */
     int tile_g;              /* ordinates per sweep work item used by this solve          */
     int rows_per_step;       /* X-Y sweep: grid rows a lane advances per wavefront step    */
-                             /* (4, or 2 when the tile_g = -1 autotuner finds it faster    */
-                             /* in the moment modes); 0 for 3D grids                       */
+                             /* (4, or 1 or 2 when the tile_g = -1 autotuner finds it      */
+                             /* faster in the moment modes); 0 for 3D grids                */
     double balance_max;      /* X-Y moment modes: largest relative particle-balance error  */
                              /* of each sample's last sweep (rom_get_balance); NaN when    */
                              /* not computed (3D, dense operator mode)                     */

@@ -364,11 +364,12 @@ int source_mode(const rom_ctx *ctx)
 }
 
 // rows per wavefront step of the X-Y sweep: forced by the option, else the autotuned
-// value (moment modes), else 4
+// value (moment modes), else 4; 1 is the one-row kernel (sweep2d_row.cuh)
 int choose_rows(const rom_ctx *ctx)
 {
     if (ctx->dim != 2 || source_mode(ctx) == 0) return 4;
-    if (ctx->opt.rows_per_step == 2 || ctx->opt.rows_per_step == 4) return ctx->opt.rows_per_step;
+    if (ctx->opt.rows_per_step == 1 || ctx->opt.rows_per_step == 2 || ctx->opt.rows_per_step == 4)
+        return ctx->opt.rows_per_step;
     if (ctx->opt.tile_g == -1 && ctx->tuned_h > 0) return ctx->tuned_h;
     return 4;
 }
@@ -822,6 +823,13 @@ cudaError_t launch_xy_sweep(const rom_ctx *ctx, const romk::SweepArgs &sa, int G
 {
     const int L = (ctx->I + romk::kCols - 1) / romk::kCols;
     const int nwarps = (L + 31) / 32;
+    if (H == 1) {
+        if (batch(ctx))
+            return romk::launch_sweep2d_row_batch(sa, (int)ctx->items.size(), nwarps, G,
+                                                  ctx->opt.scheme, ctx->MOM, st);
+        return romk::launch_sweep2d_row(sa, (int)ctx->items.size(), nwarps, G, ctx->opt.scheme,
+                                        ctx->homog, ctx->MOM, st);
+    }
     if (batch(ctx))
         return romk::launch_sweep2d_batch(sa, (int)ctx->items.size(), nwarps, G, ctx->opt.scheme,
                                           ctx->MOM, H, st);
@@ -951,16 +959,17 @@ int ensure_state(rom_ctx *ctx);
 int init_state(rom_ctx *ctx);
 
 // tile_g = -1: time the sweep kernel of every candidate work-item size G and
-// rows per wavefront step H (2 only in the moment modes) on the current problem
-// (three sweeps after one warm-up, from the initial source) and keep the fastest.
+// rows per wavefront step H (1 and 2 only in the moment modes) on the current
+// problem (three sweeps after one warm-up, from the initial source) and keep the
+// fastest.
 int autotune_g(rom_ctx *ctx)
 {
     const int cap = source_mode(ctx) == 0 ? 2 : 4;
     float best_ms = 0.f;
     int best = 0, best_h = 4, rc;
-    const int want_h = source_mode(ctx) == 0 ? 4 : ctx->opt.rows_per_step;  // 0: both
-    for (int cand = 0; cand < 6; ++cand) {
-        const int G = (1 << (cand >> 1)), H = (cand & 1) ? 2 : 4;
+    const int want_h = source_mode(ctx) == 0 ? 4 : ctx->opt.rows_per_step;  // 0: every H
+    for (int cand = 0; cand < 9; ++cand) {
+        const int G = 1 << (cand / 3), H = 1 << (cand % 3);  // H = 1, 2, 4
         if (G > cap || (want_h != 0 && H != want_h)) continue;
         ctx->opt.tile_g = G;
         if ((rc = build_items(ctx))) return rc;
@@ -1231,8 +1240,9 @@ int rom_set_options(rom_ctx *ctx, const rom_options *opt)
         return fail(ctx, ROM_ERR_INVALID_ARG, "dense_source must be 0 or 1");
     if (opt->dense_precision != 0 && opt->dense_precision != 1)
         return fail(ctx, ROM_ERR_INVALID_ARG, "dense_precision must be 0 or 1");
-    if (opt->rows_per_step != 0 && opt->rows_per_step != 2 && opt->rows_per_step != 4)
-        return fail(ctx, ROM_ERR_INVALID_ARG, "rows_per_step must be 0, 2 or 4");
+    if (opt->rows_per_step != 0 && opt->rows_per_step != 1 && opt->rows_per_step != 2 &&
+        opt->rows_per_step != 4)
+        return fail(ctx, ROM_ERR_INVALID_ARG, "rows_per_step must be 0, 1, 2 or 4");
     if (opt->diverge_window < 0) return fail(ctx, ROM_ERR_INVALID_ARG, "diverge_window < 0");
     if (!(opt->wait_timeout_ms > 0.0) || !(opt->wait_timeout_ms <= 6e5))
         return fail(ctx, ROM_ERR_INVALID_ARG, "wait_timeout_ms must be in (0, 600000]");

@@ -313,6 +313,11 @@ cudaError_t launch_sweep2d_rows2(const SweepArgs &a, int n_items, int nwarps, in
 // batches of several grids (a.grids, a.soff set): mom 1 or 3, rows 2 or 4
 cudaError_t launch_sweep2d_batch(const SweepArgs &a, int n_items, int nwarps, int G, int scheme,
                                  int mom, int rows, cudaStream_t st);
+// one grid row per wavefront step (sweep2d_row.cuh): moment modes (mom 1 or 3)
+cudaError_t launch_sweep2d_row(const SweepArgs &a, int n_items, int nwarps, int G, int scheme,
+                               bool homog, int mom, cudaStream_t st);
+cudaError_t launch_sweep2d_row_batch(const SweepArgs &a, int n_items, int nwarps, int G,
+                                     int scheme, int mom, cudaStream_t st);
 cudaError_t launch_sweep3d(const Sweep3Args &a, int n_ctas, int nwarps, int G, int scheme,
                            cudaStream_t st);
 int sweep3d_ctas_per_sm(int nwarps, int G);

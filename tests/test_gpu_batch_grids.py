@@ -90,7 +90,7 @@ def oracle_batch(grids, per_grid, sets, **kw):
 
 
 @pytest.mark.parametrize("scheme", ["dd", "step"])
-@pytest.mark.parametrize("rows", [4, 2])
+@pytest.mark.parametrize("rows", [4, 2, 1])
 @pytest.mark.parametrize("tile_g", [1, 2, 4])
 def test_mixed_grids_fixed_k_parity(rom, scheme, rows, tile_g):
     """Three grids (ragged, two warps wide, exact tiles) with uneven M per sample."""

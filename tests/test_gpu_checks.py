@@ -46,10 +46,11 @@ def _ctx(R, I, J, bounds, st, ss, q, sets, inflow=None, per_ordinate=None, **opt
 @pytest.mark.parametrize("inflow", ["vacuum", "isotropic", "per_ordinate"])
 @pytest.mark.parametrize("grid", [(37, 29), (70, 9), (300, 41)], ids=["37x29", "70x9", "300x41"])
 @pytest.mark.parametrize("tile_g", [1, 2, 4])
-def test_balance_and_leakage_match_oracle(rom, scheme, inflow, grid, tile_g):
+@pytest.mark.parametrize("rows", [4, 1])
+def test_balance_and_leakage_match_oracle(rom, scheme, inflow, grid, tile_g, rows):
     """Ragged grids, random media, random inflow: the GPU's net leakage of the
     last sweep equals the oracle's (FP32 sweep against FP64), and its balance
-    closes to FP32 rounding."""
+    closes to FP32 rounding (blocked and one-row sweep kernels)."""
     I, J = grid
     bounds = (0.0, 1.3, -0.2, 0.9)
     st, ss, q = W.random_medium(I, J, seed=I + 7 * J)
@@ -59,7 +60,7 @@ def test_balance_and_leakage_match_oracle(rom, scheme, inflow, grid, tile_g):
     per = W.random_inflow(I, J, seed=4, per_ordinate_M=17) if inflow == "per_ordinate" else None
     K = 5
     ctx = _ctx(rom, I, J, bounds, st, ss, q, sets, inflow=iso, per_ordinate=per,
-               scheme=rom.SCHEME[scheme], fixed_iters=K, tile_g=tile_g)
+               scheme=rom.SCHEME[scheme], fixed_iters=K, tile_g=tile_g, rows_per_step=rows)
     stats = ctx.solve()
     leak, bal, mn = ctx.balance()
     phi = np.stack([ctx.scalar_flux(k) for k in range(2)])
@@ -143,7 +144,7 @@ def test_divergence_detected(rom):
     ctx.close()
 
 
-@pytest.mark.parametrize("case", ["xy", "xy_one_warp", "3d"])
+@pytest.mark.parametrize("case", ["xy", "xy_one_warp", "xy_one_row", "3d"])
 def test_bounded_waits_report_timeout(rom, case):
     """test_stall_waits makes every sweep warp wait on an mbarrier that nothing
     completes; with a 5 ms bound the sweep gives up, raises its error word and
@@ -158,7 +159,9 @@ def test_bounded_waits_report_timeout(rom, case):
         I, J = (300, 40) if case == "xy" else (40, 30)
         ctx.set_grid(I, J, (0, 1, 0, 1), 1.0, 0.5, 1.0)
         ctx.set_ordinates_seed(3, [1], [2])
-    ctx.set_options(fixed_iters=2, test_stall_waits=1, wait_timeout_ms=5.0, check_every=1)
+    rows = 1 if case == "xy_one_row" else 0
+    ctx.set_options(fixed_iters=2, test_stall_waits=1, wait_timeout_ms=5.0, check_every=1,
+                    rows_per_step=rows)
     with pytest.raises(rom.RomError) as e:
         ctx.solve()
     assert e.value.code == -8

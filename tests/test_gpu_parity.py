@@ -101,12 +101,13 @@ GRIDS = [
 @pytest.mark.parametrize("scheme", ["dd", "step"])
 @pytest.mark.parametrize("grid", GRIDS, ids=[f"{g[0]}x{g[1]}" for g in GRIDS])
 @pytest.mark.parametrize("homog", [True, False])
-@pytest.mark.parametrize("rows", [4, 2])
+@pytest.mark.parametrize("rows", [4, 2, 1])
 @pytest.mark.parametrize("tile_g", [1, 2, 4])
 def test_fixed_k_parity_random_directions(rom, scheme, grid, homog, rows, tile_g):
-    """rows = grid rows a lane advances per wavefront step, tile_g = ordinates per
-    work item (every compiled kernel shape); ragged grids leave a partial lane and
-    partial row blocks, and a 300-wide grid spans two warps."""
+    """rows = grid rows a lane advances per wavefront step (1: the one-row kernel
+    with the in-lane prefix of affine maps), tile_g = ordinates per work item
+    (every compiled kernel shape); ragged grids leave a partial lane and partial
+    row blocks, and a 300-wide grid spans two warps."""
     I, J, bounds = grid
     st, ss, q = W.random_medium(I, J, seed=I * 31 + J)
     if homog:
@@ -126,7 +127,7 @@ def test_fixed_k_parity_random_directions(rom, scheme, grid, homog, rows, tile_g
 
 
 @pytest.mark.parametrize("tile_g", [-1, 1, 2, 4])
-@pytest.mark.parametrize("rows", [0, 2, 4])
+@pytest.mark.parametrize("rows", [0, 1, 2, 4])
 def test_work_item_size_does_not_change_results(rom, tile_g, rows):
     I, J = 70, 45
     bounds = (0, 1, 0, 1)
@@ -143,7 +144,7 @@ def test_work_item_size_does_not_change_results(rom, tile_g, rows):
     assert gpu["stats"]["rows_per_step"] == (rows if rows else
                                              (gpu["stats"]["rows_per_step"] if tile_g == -1
                                               else 4))
-    assert gpu["stats"]["rows_per_step"] in (2, 4)
+    assert gpu["stats"]["rows_per_step"] in (1, 2, 4)
 
 
 # ------------------------------------------------------ converged parity
@@ -181,7 +182,7 @@ def test_dom_uniform_and_gauss_parity(rom):
         assert rel(phi, ref["phi"][0]) < TOL, kind
 
 
-@pytest.mark.parametrize("rows", [4, 2])
+@pytest.mark.parametrize("rows", [4, 2, 1])
 def test_linear_kernel_parity(rom, rows):
     """Linear anisotropic kernel g = 0.9 (eq. anisotropic kernel): the GPU's
     3-moment source against the oracle's dense w_l' P(u_l', u_l) contraction."""
@@ -208,17 +209,24 @@ def test_equilibrium_inflow(rom):
     np.testing.assert_allclose(gpu["phi"], val, rtol=2e-6)
 
 
-def test_inflow_isotropic_and_per_ordinate_parity(rom):
+@pytest.mark.parametrize("rows", [4, 1])
+@pytest.mark.parametrize("homog", [False, True])
+def test_inflow_isotropic_and_per_ordinate_parity(rom, rows, homog):
     I, J = 33, 27
     bounds = (0, 1, 0, 1)
     st, ss, q = W.random_medium(I, J, seed=55)
+    if homog:
+        st = np.full((J, I), 2.5)
+        ss = np.minimum(ss, 2.0)
     sets = [O.Ordinates(*W.random_directions(9, seed=56, weights="random"))]
     iso = W.random_inflow(I, J, seed=57)
-    gpu = gpu_solve(rom, I, J, bounds, st, ss, q, sets=sets, inflow=iso, fixed_iters=5)
+    gpu = gpu_solve(rom, I, J, bounds, st, ss, q, sets=sets, inflow=iso, fixed_iters=5,
+                    rows_per_step=rows)
     ref = O.solve_xy(I, J, bounds, st, ss, q, sets, inflow=iso, fixed_iters=5)
     assert rel(gpu["phi"][0], ref["phi"][0]) < TOL
     per = W.random_inflow(I, J, seed=58, per_ordinate_M=9)
-    gpu = gpu_solve(rom, I, J, bounds, st, ss, q, sets=sets, inflow_ord=per, fixed_iters=5)
+    gpu = gpu_solve(rom, I, J, bounds, st, ss, q, sets=sets, inflow_ord=per, fixed_iters=5,
+                    rows_per_step=rows)
     ref = O.solve_xy(I, J, bounds, st, ss, q, sets, inflow=per, inflow_per_ordinate=True,
                      fixed_iters=5)
     assert rel(gpu["phi"][0], ref["phi"][0]) < TOL
