@@ -187,23 +187,34 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def traffic_record(name, source_file, samples_now):
+def traffic_record(name, source_file, samples_now, shape=None):
     """DRAM bytes of one full launch (every sample active) of a kernel, from the
     committed ncu capture profiles/<name>.traffic.json, scaled from the captured
     batch to samples_now samples; None when the kernel source differs from the
-    one captured (sha256) or no record exists."""
+    one captured (sha256) or no record exists.  Records with a "shapes" table
+    hold one capture per work-item shape (e.g. "G2H1": 2 ordinates per item, one
+    row per step), each with the source file it was built from."""
     import hashlib
     tpath = os.path.join(ROOT, "profiles", name + ".traffic.json")
-    spath = os.path.join(ROOT, "paper_2407_12527_gb300", "csrc", source_file)
     if not os.path.exists(tpath):
         return None
     with open(tpath) as f:
         tr = json.load(f)
+    if "shapes" in tr:
+        rec = tr["shapes"].get(shape)
+        if rec is None:
+            return None
+        source_file = rec["source_file"]
+    else:
+        rec = tr
+    if source_file is None:
+        return None
+    spath = os.path.join(ROOT, "paper_2407_12527_gb300", "csrc", source_file)
     with open(spath, "rb") as f:
         digest = hashlib.sha256(f.read()).hexdigest()
-    if tr.get("source_sha256") != digest:
+    if rec.get("source_sha256") != digest:
         return None
-    return tr["dram_bytes_per_launch"] * samples_now / tr["samples"]
+    return rec["dram_bytes_per_launch"] * samples_now / tr["samples"]
 
 
 def measured_hbm_gbs():
@@ -463,13 +474,16 @@ def run_ours(args):
                                         1e3 * src_ms / max(src_n, 1), None)
     else:
         achieved = sweep_upd * fpu / (sweep_ms / 1e3) / 1e12
-        kernel_name = "sweep3d_kernel (K9)" if WL.dim == 3 else "sweep2d_kernel (K1)"
+        kernel_name = ("sweep3d_kernel (K9)" if WL.dim == 3 else
+                       "sweep2d_row_kernel (K1, one row per step)" if s["rows_per_step"] == 1
+                       else "sweep2d_kernel (K1, %d rows per step)" % s["rows_per_step"])
         kernel_name, n_l, avg_us, fu = (kernel_name, sweep_n, 1e3 * sweep_ms / max(sweep_n, 1), fpu)
     # DRAM bytes of one full launch from the committed ncu captures, used only
     # while the kernel source is the one that was captured
     traffic = None
-    if WL.name == "point_source" and s["tile_g"] == 2 and s["rows_per_step"] == 4:
-        traffic = traffic_record("sweep2d_point_source_256", "sweep2d_impl.cuh", WL.samples)
+    if WL.name == "point_source":
+        traffic = traffic_record("sweep2d_point_source_256", None, WL.samples,
+                                 shape="G%dH%d" % (s["tile_g"], s["rows_per_step"]))
     elif WL.name == "lognormal_cube" and s["tile_g"] == 2:
         traffic = traffic_record("sweep3d_lognormal_cube_128", "sweep3d.cu", WL.samples)
     elif WL.name == "checkerboard" and s["tile_g"] == 4 and s["rows_per_step"] == 2:
@@ -516,7 +530,7 @@ def run_ours(args):
                     "kernel": kernel_name, "launches": n_l, "avg_launch_us": avg_us,
                     "flop_per_update": fu,
                     "sweep_avg_launch_us": 1e3 * sweep_ms / max(sweep_n, 1),
-                    "tile_g": s["tile_g"],
+                    "tile_g": s["tile_g"], "rows_per_step": s["rows_per_step"],
                     "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 flop x 2070 MHz"}
         if "sweep" in kernel_name and sweep_ms > 0:
             # the same kernel against HBM: per cell and sample the source moments read
