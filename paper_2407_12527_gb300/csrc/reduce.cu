@@ -28,6 +28,8 @@
 // average:  phi_bar = (1/t) sum_s phi^{xi_s} in FP64 (Sec. 4.1).
 #include <math.h>
 
+#include <algorithm>
+
 #include "rom_internal.cuh"
 
 namespace romk {
@@ -83,71 +85,83 @@ __global__ void __launch_bounds__(256) combine_kernel(const CombineArgs A0)
         if (A0.sigma_t) A.sigma_t = A0.sigma_t + g.off;
         base = A0.soff[s];
     }
-    const long long cells = A.cells;  // a multiple of 8: every thread owns one 32-byte sector
+    const long long cells = A.cells;  // a multiple of 8: a thread takes whole 32-byte sectors
     float *phi = A.phi + base;
     float *src = A.src + base;
     float d2f = 0.f, n2f = 0.f, mn = INFINITY, a1f = 0.f, b0f = 0.f, b1f = 0.f, b2f = 0.f;
-    for (long long v = 8 * ((long long)blockIdx.x * blockDim.x + threadIdx.x); v < cells;
-         v += 8LL * gridDim.x * blockDim.x) {
-        float acc[MOM][8];
-        float old[8], ss[8], qq[8], out[8], st[8];
-        ld8_volatile(phi + v, old);
-        ldg8(A.sigma_s + v, ss);
-        ldg8(A.q + v, qq);
-        if (A.balance) {
-            // the source moments of the previous iterate (the sweep's input) and
-            // sigma_T phi of the new one, for the particle balance; padding
-            // columns hold phi = 0 and sigma_S = q = 0
-            if (A.sigma_t) ldg8(A.sigma_t + v, st);
+    // KS sectors per thread and pass, all loaded before any store (the loads and
+    // stores are ordered volatile accesses): KS times the bytes in flight per thread
+    constexpr int KS = MOM == 1 ? 2 : 1;
+    const long long stride = 8LL * gridDim.x * blockDim.x;
+    for (long long v0 = 8 * ((long long)blockIdx.x * blockDim.x + threadIdx.x); v0 < cells;
+         v0 += KS * stride) {
+        float acc[KS][MOM][8], old[KS][MOM][8], ss[KS][8], qq[KS][8], st[KS][8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) b0f += fmaf(ss[e], old[e], qq[e]);
-            if (MOM == 3) {
-                float o1[8], o2[8];
-                ld8_volatile(phi + cells + v, o1);
-                ld8_volatile(phi + 2 * cells + v, o2);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    b1f = fmaf(A.g * ss[e], o1[e], b1f);
-                    b2f = fmaf(A.g * ss[e], o2[e], b2f);
-                }
+        for (int k = 0; k < KS; ++k) {
+            const long long v = v0 + k * stride;
+            if (v >= cells) continue;
+            ld8_volatile(phi + v, old[k][0]);
+            if (MOM == 3 && A.balance) {
+                ld8_volatile(phi + cells + v, old[k][MOM == 3 ? 1 : 0]);
+                ld8_volatile(phi + 2 * cells + v, old[k][MOM == 3 ? 2 : 0]);
             }
-            // the accumulated moments are read below; sigma_T phi is added there
-            if (!A.sigma_t)
 #pragma unroll
-                for (int e = 0; e < 8; ++e) st[e] = A.sigma_t_homog;
+            for (int m = 0; m < MOM; ++m) ld8_volatile(A.acc + base + m * cells + v, acc[k][m]);
+            ldg8(A.sigma_s + v, ss[k]);
+            ldg8(A.q + v, qq[k]);
+            if (A.balance && A.sigma_t) ldg8(A.sigma_t + v, st[k]);
         }
-        {  // the sample's accumulated moments, cleared for the next sweep
-            float zero[8];
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+            const long long v = v0 + k * stride;
+            if (v >= cells) continue;
+            if (A.balance) {
+                // the source moments of the previous iterate (the sweep's input) and
+                // sigma_T phi of the new one, for the particle balance; padding
+                // columns hold phi = 0 and sigma_S = q = 0
+#pragma unroll
+                for (int e = 0; e < 8; ++e) b0f += fmaf(ss[k][e], old[k][0][e], qq[k][e]);
+                if (MOM == 3) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        b1f = fmaf(A.g * ss[k][e], old[k][MOM == 3 ? 1 : 0][e], b1f);
+                        b2f = fmaf(A.g * ss[k][e], old[k][MOM == 3 ? 2 : 0][e], b2f);
+                    }
+                }
+                if (!A.sigma_t)
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) st[k][e] = A.sigma_t_homog;
+            }
+            // per-element squares in FP32 (a few terms per thread), norms in FP64 below
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float dd = acc[k][0][e] - old[k][0][e];
+                d2f = fmaf(dd, dd, d2f);
+                n2f = fmaf(acc[k][0][e], acc[k][0][e], n2f);
+                if (A.balance) a1f = fmaf(st[k][e], acc[k][0][e], a1f);  // sigma_T phi
+                // padding columns (x >= I) hold phi = 0 and would hide a negative min
+                if ((v % A.NXP) + e < A.I) mn = fminf(mn, acc[k][0][e]);
+            }
+            // the accumulated moments cleared for the next sweep; phi and the next
+            // source moments written
+            float zero[8], out[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) zero[e] = 0.f;
 #pragma unroll
             for (int m = 0; m < MOM; ++m) {
-                float *p = A.acc + base + m * cells + v;
-                ld8_volatile(p, acc[m]);
-                stg8(p, zero);
+                stg8(A.acc + base + m * cells + v, zero);
+                stg8(phi + m * cells + v, acc[k][m]);
             }
-        }
-        // per-element squares in FP32 (a few terms per thread), norms in FP64 below
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const float dd = acc[0][e] - old[e];
-            d2f = fmaf(dd, dd, d2f);
-            n2f = fmaf(acc[0][e], acc[0][e], n2f);
-            if (A.balance) a1f = fmaf(st[e], acc[0][e], a1f);  // sigma_T phi
-            // padding columns (x >= I) hold phi = 0 and would hide a negative min
-            if ((v % A.NXP) + e < A.I) mn = fminf(mn, acc[0][e]);
-        }
+            for (int e = 0; e < 8; ++e) out[e] = fmaf(ss[k][e], acc[k][0][e], qq[k][e]);
+            stg8(src + v, out);
+            if (MOM == 3) {
 #pragma unroll
-        for (int m = 0; m < MOM; ++m) stg8(phi + m * cells + v, acc[m]);
+                for (int m = 1; m < 3; ++m) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) out[e] = fmaf(ss[e], acc[0][e], qq[e]);
-        stg8(src + v, out);
-        if (MOM == 3) {
-#pragma unroll
-            for (int m = 1; m < 3; ++m) {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) out[e] = A.g * ss[e] * acc[m][e];
-                stg8(src + m * cells + v, out);
+                    for (int e = 0; e < 8; ++e) out[e] = A.g * ss[k][e] * acc[k][m][e];
+                    stg8(src + m * cells + v, out);
+                }
             }
         }
     }
@@ -456,7 +470,10 @@ int blocks_for(long long n, int threads)
 
 cudaError_t launch_combine(const CombineArgs &a, cudaStream_t st)
 {
-    const dim3 grid(a.chunks, a.S), block(256);
+    // enough blocks for every thread to take KS sectors (combine_kernel), at most chunks
+    const long long ks = a.MOM == 1 ? 2 : 1;
+    const long long need = (a.cells / 8 + 256 * ks - 1) / (256 * ks);
+    const dim3 grid((unsigned)std::max(1LL, std::min((long long)a.chunks, need)), a.S), block(256);
     if (a.MOM == 1) combine_kernel<1><<<grid, block, 0, st>>>(a);
     else if (a.MOM == 3) combine_kernel<3><<<grid, block, 0, st>>>(a);
     else return cudaErrorInvalidValue;
