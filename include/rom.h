@@ -106,8 +106,8 @@ typedef struct rom_options {
                      /* ROM_ERR_UNSUPPORTED)                                               */
     int rows_per_step; /* X-Y sweep: grid rows a lane advances per wavefront step; 0 = 4,  */
                      /* or the measured choice with tile_g = -1 (1, 2 or 4); 1, 2 or 4     */
-                     /* forces it (1 and 2 only in the isotropic and linear-kernel moment  */
-                     /* modes, the dense operator mode runs 4; 1 solves each lane's 8-cell */
+                     /* forces it (2 only in the isotropic and linear-kernel moment modes: */
+                     /* the dense operator mode runs 4 then; 1 solves each lane's 8-cell   */
                      /* upwind recurrence as a prefix of affine maps); other values are    */
                      /* ROM_ERR_INVALID_ARG                                                */
     int diverge_window; /* 16: a sample whose change ||phi^k - phi^{k-1}||_2 grew in this  */
@@ -139,7 +139,7 @@ typedef struct rom_stats {
     int tile_g;              /* ordinates per sweep work item used by this solve          */
     int rows_per_step;       /* X-Y sweep: grid rows a lane advances per wavefront step    */
                              /* (4, or 1 or 2 when the tile_g = -1 autotuner finds it      */
-                             /* faster in the moment modes); 0 for 3D grids                */
+                             /* faster; 2 only in the moment modes); 0 for 3D grids        */
     double balance_max;      /* X-Y moment modes: largest relative particle-balance error  */
                              /* of each sample's last sweep (rom_get_balance); NaN when    */
                              /* not computed (3D, dense operator mode)                     */

@@ -367,7 +367,12 @@ int source_mode(const rom_ctx *ctx)
 // value (moment modes), else 4; 1 is the one-row kernel (sweep2d_row.cuh)
 int choose_rows(const rom_ctx *ctx)
 {
-    if (ctx->dim != 2 || source_mode(ctx) == 0) return 4;
+    if (ctx->dim != 2) return 4;
+    if (source_mode(ctx) == 0) {  // dense operator mode: the 4-row or the one-row kernel
+        if (ctx->opt.rows_per_step == 1) return 1;
+        if (ctx->opt.tile_g == -1 && ctx->tuned_h > 0) return ctx->tuned_h;
+        return 4;
+    }
     if (ctx->opt.rows_per_step == 1 || ctx->opt.rows_per_step == 2 || ctx->opt.rows_per_step == 4)
         return ctx->opt.rows_per_step;
     if (ctx->opt.tile_g == -1 && ctx->tuned_h > 0) return ctx->tuned_h;
@@ -967,10 +972,12 @@ int autotune_g(rom_ctx *ctx)
     const int cap = source_mode(ctx) == 0 ? 2 : 4;
     float best_ms = 0.f;
     int best = 0, best_h = 4, rc;
-    const int want_h = source_mode(ctx) == 0 ? 4 : ctx->opt.rows_per_step;  // 0: every H
+    const bool dense = source_mode(ctx) == 0;
+    // 0: every H (dense operator mode: 1 and 4; 2 there means 4)
+    const int want_h = dense && ctx->opt.rows_per_step == 2 ? 4 : ctx->opt.rows_per_step;
     for (int cand = 0; cand < 9; ++cand) {
         const int G = 1 << (cand / 3), H = 1 << (cand % 3);  // H = 1, 2, 4
-        if (G > cap || (want_h != 0 && H != want_h)) continue;
+        if (G > cap || (want_h != 0 && H != want_h) || (dense && H == 2)) continue;
         ctx->opt.tile_g = G;
         if ((rc = build_items(ctx))) return rc;
         if ((rc = ensure_state(ctx))) return rc;  // phi, sources, accumulators

@@ -13,8 +13,6 @@
 #ifndef SWEEP2D_BATCH
 #define SWEEP2D_BATCH 0  // 1: the kernels of batches of several grids (SweepArgs::grids)
 #endif
-#include <cuda_bf16.h>
-
 #include "rom_internal.cuh"
 
 namespace romk {
@@ -141,31 +139,6 @@ __device__ __forceinline__ void put8(float *p, const float (&v)[kCols])
 {
     red8(p, v);
 }
-// psi of 8 cells as BF16 parts in one 32-byte sector, [8 hi | 8 lo] (the byte
-// layout of the FP32 array): hi = v rounded to the nearest BF16 on its bit
-// pattern (add half a BF16 unit, clear the low 16 bits; ties away from zero;
-// two packed by one byte permute), lo = bf16_rn(v - hi) (the difference is exact
-// in FP32; two converted by one packed conversion).  hi + lo carries 16
-// significant bits of v, and lo has either sign, so the lo * lo term the
-// product drops has no bias.
-__device__ __forceinline__ void st8_split(uint32_t *psi2, long long off, const float (&v)[kCols])
-{
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const uint32_t b0 = (__float_as_uint(v[2 * e]) + 0x8000u) & 0xFFFF0000u;
-        const uint32_t b1 = (__float_as_uint(v[2 * e + 1]) + 0x8000u) & 0xFFFF0000u;
-        h[e] = __byte_perm(b0, b1, 0x7632);
-        const float r0 = v[2 * e] - __uint_as_float(b0);
-        const float r1 = v[2 * e + 1] - __uint_as_float(b1);
-        const __nv_bfloat162 lo2 = __floats2bfloat162_rn(r0, r1);
-        l[e] = *reinterpret_cast<const uint32_t *>(&lo2);
-    }
-    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(psi2 + off), "r"(h[0]),
-                 "r"(h[1]), "r"(h[2]), "r"(h[3]), "r"(l[0]), "r"(l[1]), "r"(l[2]), "r"(l[3])
-                 : "memory");
-}
-
 // Per-ordinate constants of a work item, grouped in packs.
 template <int G>
 struct OrdPacks {

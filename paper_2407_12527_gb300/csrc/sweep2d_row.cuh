@@ -117,8 +117,12 @@ __device__ __forceinline__ bool row_never_wait(unsigned long long *b, unsigned l
     }
 }
 
-// arrays read per cell: the source moments, and sigma_T when it varies
-__host__ __device__ constexpr int row_arrays(int mom, bool homog) { return mom + (homog ? 0 : 1); }
+// arrays read per cell: the source moments (dense mode: one source per ordinate of
+// the item), and sigma_T when it varies
+__host__ __device__ constexpr int row_arrays(int mom, int g, bool homog)
+{
+    return (mom == 0 ? g : mom) + (homog ? 0 : 1);
+}
 // steps between the load of a row and its use (registers: 8 floats per array and slot)
 __host__ __device__ constexpr int row_pd(int na, int g)
 {
@@ -131,7 +135,8 @@ __device__ __forceinline__ void row_item(const SweepArgs &A, const SweepItem &it
     using T = typename RowPack<G>::T;
     constexpr int N = RowPack<G>::N;
     constexpr int PER = G == 1 ? 1 : 2;  // ordinates per pack
-    constexpr int NA = row_arrays(MOM, HOMOG);
+    constexpr int NA = row_arrays(MOM, G, HOMOG);
+    constexpr int NS = MOM == 0 ? G : MOM;  // source arrays (the rest: sigma_T)
     constexpr int PD = row_pd(NA, G);
     const int g = threadIdx.x;
     const int nwarps = MULTI ? (int)(blockDim.x >> 5) : 1;
@@ -239,11 +244,15 @@ __device__ __forceinline__ void row_item(const SweepArgs &A, const SweepItem &it
         lk = rsplat<T>(0.f);
     }
 
-    // the item's arrays: source moments of its sample, sigma_T; its accumulator
-    const long long soff = A.soff ? A.soff[it.sample] : (long long)it.sample * MOM * A.cells;
+    // the item's arrays: source moments of its sample (dense mode: the source of each
+    // of its ordinates), sigma_T; its accumulator
+    constexpr int NOUT = MOM == 0 ? 1 : MOM;
+    const long long soff = A.soff ? A.soff[it.sample] : (long long)it.sample * NOUT * A.cells;
     const float *arr[NA];
 #pragma unroll
-    for (int m = 0; m < MOM; ++m) arr[m] = A.src + soff + (long long)m * A.cells + col0;
+    for (int m = 0; m < NS; ++m)
+        arr[m] = MOM == 0 ? A.src + (long long)ord[m] * A.cells + col0
+                          : A.src + soff + (long long)m * A.cells + col0;
     if constexpr (!HOMOG) arr[NA - 1] = A.sigma_t + col0;
     float *part = A.part + soff + col0;
     const long long rs = yneg ? -(long long)A.NXP : (long long)A.NXP;
@@ -296,6 +305,10 @@ __device__ __forceinline__ void row_item(const SweepArgs &A, const SweepItem &it
 #pragma unroll
                     for (int p = 0; p < N; ++p) {
                         T S = rsplat<T>(B[0][r]);
+                        if constexpr (MOM == 0) {  // the pack's own per-ordinate sources
+                            rset(S, 0, B[(p * PER) % NS][r]);
+                            if constexpr (PER == 2) rset(S, 1, B[(p * PER + 1) % NS][r]);
+                        }
                         if constexpr (MOM == 3)
                             S = rfma(cc[p], rsplat<T>(B[1][r]), rfma(cs[p], rsplat<T>(B[2][r]), S));
                         T Y;
@@ -330,6 +343,7 @@ __device__ __forceinline__ void row_item(const SweepArgs &A, const SweepItem &it
                 }
                 // pass 2: the cells with their true incoming flux
                 float v0[kCols], v1[kCols], v2[kCols];
+                float psi_row[MOM == 0 ? G : 1][kCols];  // dense mode: psi_c of each ordinate
                 T xprev[N];
 #pragma unroll
                 for (int p = 0; p < N; ++p) xprev[p] = xin[p];
@@ -344,6 +358,16 @@ __device__ __forceinline__ void row_item(const SweepArgs &A, const SweepItem &it
                         // DD: x_in + x_out = 2 psi_c; step: x_out = psi_c
                         const T m = SCHEME == 0 ? radd(xprev[p], xn) : xn;
                         a0 = rfma(cw[p], m, a0);
+                        if constexpr (MOM == 0) {
+                            const T pc = SCHEME == 0 ? rmul(m, rsplat<T>(0.5f)) : xn;
+                            const bool rl1 = !RAGGED || real[rr];
+                            if constexpr (PER == 2) {
+                                psi_row[(2 * p) % G][r] = rl1 ? reinterpret_cast<const float2 &>(pc).x : 0.f;
+                                psi_row[(2 * p + 1) % G][r] = rl1 ? reinterpret_cast<const float2 &>(pc).y : 0.f;
+                            } else {
+                                psi_row[0][r] = rl1 ? reinterpret_cast<const float &>(pc) : 0.f;
+                            }
+                        }
                         if constexpr (MOM == 3) {
                             a1 = rfma(cwc[p], m, a1);
                             a2 = rfma(cws[p], m, a2);
@@ -363,6 +387,15 @@ __device__ __forceinline__ void row_item(const SweepArgs &A, const SweepItem &it
 #pragma unroll
                 for (int p = 0; p < N; ++p) xo[p] = xprev[p];
                 rred8(part + row, v0);
+                if constexpr (MOM == 0) {  // psi of every ordinate of the item, for the contraction
+#pragma unroll
+                    for (int k = 0; k < G; ++k)
+                        if (k < it.n) {
+                            const long long off = (long long)ord[k] * A.cells + row + col0;
+                            if (A.psi_split) st8_split(A.psi_split, off, psi_row[k]);
+                            else stg8(A.psi + off, psi_row[k]);
+                        }
+                }
                 if constexpr (MOM == 3) {
                     rred8(part + A.cells + row, v1);
                     rred8(part + 2 * A.cells + row, v2);

@@ -158,3 +158,57 @@ def test_dense_mode_runs_four_rows_per_step(rom):
     ref = O.solve_xy(I, J, (0, 1, 0, 1), st, ss, q, sets, kernel="hg", g=0.8, fixed_iters=3)
     for k in range(2):
         assert rel(gpu["phi"][k], ref["phi"][k]) < TOL, k
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("scheme", ["dd", "step"])
+@pytest.mark.parametrize("homog", [False, True])
+@pytest.mark.parametrize("tile_g", [1, 2])
+def test_dense_mode_one_row_sweep(rom, precision, scheme, homog, tile_g):
+    """The one-row sweep in the dense operator mode (per-ordinate sources in, psi of
+    every ordinate out as FP32 or split BF16): ragged 53 x 41 grid, uneven M, uniform
+    and varying sigma_T, both schemes, against the oracle."""
+    I, J = 53, 41
+    bounds = (0.0, 1.0, 0.0, 0.8)
+    st, ss, q = W.random_medium(I, J, seed=81, ratio_max=0.8)
+    if homog:
+        st = np.full((J, I), 2.0)
+        ss = np.minimum(ss, 1.6)
+    nz, nt = [1, 2, 2], [5, 2, 6]
+    gpu = gpu_solve(rom, I, J, bounds, st, ss, q, 83, nz, nt, fixed_iters=4,
+                    dense_precision=precision, rows_per_step=1, tile_g=tile_g,
+                    scheme=rom.SCHEME[scheme])
+    assert gpu["stats"]["rows_per_step"] == 1
+    sets = [O.rom_ordinates_xy(83, k, nz[k], nt[k]) for k in range(3)]
+    ref = O.solve_xy(I, J, bounds, st, ss, q, sets, kernel="hg", g=0.8, fixed_iters=4,
+                     scheme=scheme)
+    for k in range(3):
+        assert rel(gpu["phi"][k], ref["phi"][k]) < TOL, k
+
+
+def test_dense_mode_one_row_sweep_inflow_and_two_warps(rom):
+    """Dense mode, one-row sweep: per-ordinate inflow on every face and a 300-wide
+    grid whose rows span two warps (a shared-memory hand-off per step)."""
+    I, J = 300, 23
+    bounds = (-1.0, 2.0, 0.0, 0.5)
+    st, ss, q = W.random_medium(I, J, seed=91, ratio_max=0.8)
+    nz, nt = [1, 2], [2, 3]
+    sets = [O.rom_ordinates_xy(93, k, nz[k], nt[k]) for k in range(2)]
+    M = sum(o.M for o in sets)
+    per = W.random_inflow(I, J, seed=94, per_ordinate_M=M)
+    ctx = rom.RomContext(0)
+    ctx.set_grid(I, J, bounds, st, ss, q)
+    ctx.set_ordinates_seed(93, nz, nt)
+    ctx.set_kernel("hg", 0.8)
+    off = [0, J, 2 * J, 2 * J + I, 2 * J + 2 * I]
+    for f in range(4):
+        ctx.set_inflow_ordinates(f, np.ascontiguousarray(per[:, off[f]:off[f + 1]]))
+    ctx.set_options(fixed_iters=3, dense_precision=1, rows_per_step=1)
+    stats = ctx.solve()
+    phi = [ctx.scalar_flux(k) for k in range(2)]
+    ctx.close()
+    assert stats["rows_per_step"] == 1
+    ref = O.solve_xy(I, J, bounds, st, ss, q, sets, kernel="hg", g=0.8, fixed_iters=3,
+                     inflow=per, inflow_per_ordinate=True)
+    for k in range(2):
+        assert rel(phi[k], ref["phi"][k]) < TOL, k
