@@ -128,8 +128,9 @@ def test_degenerate_grids_in_one_batch(rom):
         assert rel(gpu["phi"][k], ref_phi[k]) < TOL, k
 
 
+@pytest.mark.parametrize("rows", [4, 1])
 @pytest.mark.parametrize("kernel", ["iso", "linear"])
-def test_mixed_grids_converged_average_and_balance(rom, kernel):
+def test_mixed_grids_converged_average_and_balance(rom, kernel, rows):
     """Seeded ROM sets of uneven size, converged solves: per-sample flux, each
     grid's sample average, and the particle balance of the last sweep."""
     per_grid = [3, 2]
@@ -137,7 +138,7 @@ def test_mixed_grids_converged_average_and_balance(rom, kernel):
     nz, nt = [1, 2, 2, 1, 3], [2, 2, 3, 4, 3]
     g = 0.7 if kernel == "linear" else 0.0
     gpu = solve_batch(rom, grids, per_grid, seed=31, nz=nz, nt=nt, kernel=kernel, g=g, tol=1e-6,
-                      max_iter=500)
+                      max_iter=500, rows_per_step=rows)
     sets = [O.rom_ordinates_xy(31, k, nz[k], nt[k]) for k in range(5)]
     ref_phi, ref_leak, ref_it = oracle_batch(grids, per_grid, sets, kernel=kernel, g=g, tol=1e-12)
     for k in range(5):

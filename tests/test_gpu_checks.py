@@ -80,7 +80,8 @@ def test_balance_and_leakage_match_oracle(rom, scheme, inflow, grid, tile_g, row
     assert stats["phi_min"] == pytest.approx(mn.min())
 
 
-def test_balance_linear_kernel_and_seeded_sets(rom):
+@pytest.mark.parametrize("rows", [4, 1])
+def test_balance_linear_kernel_and_seeded_sets(rom, rows):
     """Linear kernel (three source moments): sum_l w_l S_l = S0 sum w + S1x sum w c +
     S1y sum w s enters the balance; seeded ROM sets, converged solve."""
     p = W.example_2_1(I=50, J=44, g=0.9)
@@ -88,7 +89,7 @@ def test_balance_linear_kernel_and_seeded_sets(rom):
     ctx.set_grid(p.I, p.J, p.bounds, p.sigma_t, p.sigma_s, p.q)
     ctx.set_ordinates_seed(31, [2, 3], [2, 3])
     ctx.set_kernel("linear", 0.9)
-    ctx.set_options(tol=1e-6, max_iter=300)
+    ctx.set_options(tol=1e-6, max_iter=300, rows_per_step=rows)
     stats = ctx.solve()
     leak, bal, mn = ctx.balance()
     ctx.close()
