@@ -29,6 +29,8 @@
 // with the packed FP32x2 instructions.  Cells past I (the padding of a ragged
 // last lane) are identity maps with no moment (RAGGED instantiations only).
 #pragma once
+#include <type_traits>
+
 #include "rom_internal.cuh"
 
 namespace romk {
@@ -83,13 +85,17 @@ __device__ __forceinline__ float2 rshfl(float2 v)
     return make_float2(rshfl<DOWN>(v.x), rshfl<DOWN>(v.y));
 }
 __device__ __forceinline__ void rld8(const float *p, float (&v)[kCols]) { ldg8_early(p, v); }
-__device__ __forceinline__ void rred8(float *p, const float (&v)[kCols])
+// adds 8 moments to the accumulator; a lane that owns no cells adds nothing (the
+// reductions are predicated off, not branched around)
+__device__ __forceinline__ void rred8(float *p, const float (&v)[kCols], bool on)
 {
-    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(v[0]), "f"(v[1]),
-                 "f"(v[2]), "f"(v[3])
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t"
+                 "@q red.global.add.v4.f32 [%0], {%1,%2,%3,%4};\n\t}" ::"l"(p), "f"(v[0]),
+                 "f"(v[1]), "f"(v[2]), "f"(v[3]), "r"((unsigned)on)
                  : "memory");
-    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p + 4), "f"(v[4]), "f"(v[5]),
-                 "f"(v[6]), "f"(v[7])
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t"
+                 "@q red.global.add.v4.f32 [%0], {%1,%2,%3,%4};\n\t}" ::"l"(p + 4), "f"(v[4]),
+                 "f"(v[5]), "f"(v[6]), "f"(v[7]), "r"((unsigned)on)
                  : "memory");
 }
 __device__ __forceinline__ unsigned row_smem_u32(const void *p)
@@ -123,10 +129,11 @@ __host__ __device__ constexpr int row_arrays(int mom, int g, bool homog)
 {
     return (mom == 0 ? g : mom) + (homog ? 0 : 1);
 }
-// steps between the load of a row and its use (registers: 8 floats per array and slot)
+// steps between the load of a row and its use (registers: 8 floats per array and slot;
+// with four ordinates a deeper ring spills)
 __host__ __device__ constexpr int row_pd(int na, int g)
 {
-    return g == 4 ? (na == 1 ? 4 : (na == 2 ? 2 : 1)) : (na == 1 ? 6 : (na == 2 ? 4 : (na == 3 ? 2 : 1)));
+    return g == 4 ? (na <= 2 ? 2 : 1) : (na == 1 ? 6 : (na == 2 ? 4 : (na == 3 ? 2 : 1)));
 }
 
 template <int G, int MOM, int SCHEME, bool HOMOG, bool XNEG, bool RAGGED, bool MULTI, bool INFLOW>
@@ -248,14 +255,17 @@ __device__ __forceinline__ void row_item(const SweepArgs &A, const SweepItem &it
     // of its ordinates), sigma_T; its accumulator
     constexpr int NOUT = MOM == 0 ? 1 : MOM;
     const long long soff = A.soff ? A.soff[it.sample] : (long long)it.sample * NOUT * A.cells;
+    // A lane that owns no cells points at column 0 with row stride 0: its loads in
+    // the unchecked cycles below read a valid row, and its moments are not added.
+    const int colb = on ? col0 : 0;
     const float *arr[NA];
 #pragma unroll
     for (int m = 0; m < NS; ++m)
-        arr[m] = MOM == 0 ? A.src + (long long)ord[m] * A.cells + col0
-                          : A.src + soff + (long long)m * A.cells + col0;
-    if constexpr (!HOMOG) arr[NA - 1] = A.sigma_t + col0;
-    float *part = A.part + soff + col0;
-    const long long rs = yneg ? -(long long)A.NXP : (long long)A.NXP;
+        arr[m] = MOM == 0 ? A.src + (long long)ord[m] * A.cells + colb
+                          : A.src + soff + (long long)m * A.cells + colb;
+    if constexpr (!HOMOG) arr[NA - 1] = A.sigma_t + colb;
+    float *part = A.part + soff + colb;
+    const long long rs = !on ? 0 : (yneg ? -(long long)A.NXP : (long long)A.NXP);
     const long long row0 = yneg ? (long long)(J - 1) * A.NXP : 0;
     const int T_steps = J + L - 1;
 
@@ -280,21 +290,29 @@ __device__ __forceinline__ void row_item(const SweepArgs &A, const SweepItem &it
                      A.inflow[(long long)ord[k] * A.inflow_stride + (XNEG ? J : 0) + j]);
     }
 
-    for (int t0 = 0; t0 < T_steps; t0 += PD + 1) {
+    // A ring cycle whose steps all lie where every lane that owns cells has a row to
+    // sweep and a row to prefetch runs without the per-lane range checks, so that no
+    // branch splits its unrolled steps; the cycles of the pipeline's fill and drain
+    // keep them.  Lanes past the grid's width run the same steps on a valid row, with
+    // their moments predicated off and a zero outgoing flux, as in the checked steps;
+    // psi stores (dense mode) ask for every lane to own cells.
+    const bool full = MOM != 0 || L == 32 * nwarps;
+    auto cycle = [&](const int t0, auto checked) {
+        constexpr bool CK = decltype(checked)::value;
 #pragma unroll
         for (int u = 0; u <= PD; ++u) {
             const int t = t0 + u;
-            if (t >= T_steps) break;  // uniform over the CTA
+            if (CK && t >= T_steps) break;  // uniform over the CTA
             const int jl = t - d;
             {
                 const int jp = jl + PD;
-                if (on && jp >= 0 && jp < J)
+                if (!CK || (on && jp >= 0 && jp < J))
 #pragma unroll
                     for (int m = 0; m < NA; ++m)
                         rld8(arr[m] + row0 + (long long)jp * rs, buf[(u + PD) % (PD + 1)][m]);
             }
             T xo[N];
-            if (on && jl >= 0 && jl < J) {
+            if (!CK || (on && jl >= 0 && jl < J)) {
                 const long long row = row0 + (long long)jl * rs;
                 const float(&B)[NA][kCols] = buf[u];
                 // pass 1: each cell's map with x_in = 0, prefix over the lane's cells
@@ -385,8 +403,8 @@ __device__ __forceinline__ void row_item(const SweepArgs &A, const SweepItem &it
                     }
                 }
 #pragma unroll
-                for (int p = 0; p < N; ++p) xo[p] = xprev[p];
-                rred8(part + row, v0);
+                for (int p = 0; p < N; ++p) xo[p] = (CK || on) ? xprev[p] : rsplat<T>(0.f);
+                rred8(part + row, v0, on);
                 if constexpr (MOM == 0) {  // psi of every ordinate of the item, for the contraction
 #pragma unroll
                     for (int k = 0; k < G; ++k)
@@ -397,8 +415,8 @@ __device__ __forceinline__ void row_item(const SweepArgs &A, const SweepItem &it
                         }
                 }
                 if constexpr (MOM == 3) {
-                    rred8(part + A.cells + row, v1);
-                    rred8(part + 2 * A.cells + row, v2);
+                    rred8(part + A.cells + row, v1, on);
+                    rred8(part + 2 * A.cells + row, v2, on);
                 }
                 // x-face leakage terms (zero weights except on the boundary lanes)
 #pragma unroll
@@ -454,6 +472,10 @@ __device__ __forceinline__ void row_item(const SweepArgs &A, const SweepItem &it
             lk_s = tt;
             lk = rsplat<T>(0.f);
         }
+    };
+    for (int t0 = 0; t0 < T_steps; t0 += PD + 1) {
+        if (full && t0 >= L - 1 && t0 + 2 * PD <= J - 1) cycle(t0, std::false_type{});
+        else cycle(t0, std::true_type{});
     }
     if (A.leak) {  // the x-face sums, the outgoing y-edges; one FP64 add per warp
         leak += (double)lk_s - (double)lk_c;

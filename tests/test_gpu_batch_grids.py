@@ -19,13 +19,17 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
 
-# (I, J, bounds): ragged tiles, a grid two warps wide, one column, one row
+# (I, J, bounds): ragged tiles, a grid two warps wide, one column, one row; then
+# taller grids on which the one-row sweep reaches its unchecked middle steps
 GRIDS = [
     (37, 29, (0.0, 1.3, -0.2, 0.9)),
     (300, 23, (-1.0, 2.0, 0.0, 0.5)),
     (64, 20, (0.0, 1.0, 0.0, 0.4)),
     (1, 9, (0.0, 0.1, 0.0, 1.0)),
     (11, 1, (0.0, 1.0, 0.0, 0.1)),
+    (256, 70, (0.0, 1.0, 0.0, 0.3)),   # one warp wide: its second warp idle in the batch
+    (300, 64, (0.0, 1.2, 0.0, 0.25)),  # two warps, the second with idle lanes
+    (40, 80, (0.0, 0.5, 0.0, 1.0)),    # one warp, most lanes idle
 ]
 
 
@@ -87,6 +91,26 @@ def oracle_batch(grids, per_grid, sets, **kw):
         iters += list(ref["iters"])
         s0 += per_grid[p]
     return phi, np.array(leak), np.array(iters)
+
+
+@pytest.mark.parametrize("scheme", ["dd", "step"])
+@pytest.mark.parametrize("tile_g", [2, 4])
+def test_mixed_tall_grids_one_row_sweep(rom, scheme, tile_g):
+    """One launch over grids one and two warps wide (a whole warp idle on the
+    narrower ones) with enough rows for the unchecked middle steps."""
+    per_grid = [2, 2, 2]
+    grids, sets = make_batch([5, 6, 7], per_grid, seed0=700)
+    K = 3
+    gpu = solve_batch(rom, grids, per_grid, sets=sets, scheme=rom.SCHEME[scheme], fixed_iters=K,
+                      rows_per_step=1, tile_g=tile_g)
+    ref_phi, _, _ = oracle_batch(grids, per_grid, sets, scheme=scheme, fixed_iters=K)
+    for k in range(len(sets)):
+        assert rel(gpu["phi"][k], ref_phi[k]) < TOL, k
+    s0 = 0
+    for p in range(3):
+        want = O.rom_average(np.stack(ref_phi[s0:s0 + per_grid[p]]))
+        assert rel(gpu["avg"][p], want) < TOL, p
+        s0 += per_grid[p]
 
 
 @pytest.mark.parametrize("scheme", ["dd", "step"])

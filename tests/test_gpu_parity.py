@@ -126,6 +126,41 @@ def test_fixed_k_parity_random_directions(rom, scheme, grid, homog, rows, tile_g
     assert gpu["stats"]["tile_g"] == tile_g
 
 
+# Wide grids with enough rows for the one-row sweep's middle steps -- where every
+# lane that owns cells has a row to sweep and one to prefetch -- to run its cycles
+# without per-lane range checks (the small grids above reach them too, with most
+# lanes idle).
+WIDE_GRIDS = [
+    (256, 90, (0.0, 1.0, 0.0, 0.4)),    # one warp, every lane owns cells
+    (250, 77, (0.0, 2.0, -1.0, 0.0)),   # one warp, ragged last lane
+    (512, 100, (0.0, 1.5, 0.0, 0.3)),   # two warps, one barrier per step
+    (300, 110, (0.0, 1.2, 0.0, 0.5)),   # two warps, the second with idle lanes
+]
+
+
+@pytest.mark.parametrize("scheme", ["dd", "step"])
+@pytest.mark.parametrize("grid", WIDE_GRIDS, ids=[f"{g[0]}x{g[1]}" for g in WIDE_GRIDS])
+@pytest.mark.parametrize("homog", [True, False])
+@pytest.mark.parametrize("tile_g", [2, 4])
+@pytest.mark.parametrize("inflow", [False, True], ids=["vacuum", "inflow"])
+def test_one_row_sweep_wide_grids(rom, scheme, grid, homog, tile_g, inflow):
+    I, J, bounds = grid
+    st, ss, q = W.random_medium(I, J, seed=I + 7 * J)
+    if homog:
+        st = np.full((J, I), 1.3)
+        ss = np.minimum(ss, 1.1)
+    sets = [O.Ordinates(*W.random_directions(M, seed=300 + M, weights="random"))
+            for M in (6, 9)]
+    iso = W.random_inflow(I, J, seed=I * J) if inflow else None
+    K = 3
+    gpu = gpu_solve(rom, I, J, bounds, st, ss, q, sets=sets, scheme=rom.SCHEME[scheme],
+                    inflow=iso, fixed_iters=K, rows_per_step=1, tile_g=tile_g)
+    ref = O.solve_xy(I, J, bounds, st, ss, q, sets, scheme=scheme, inflow=iso, fixed_iters=K)
+    for k in range(len(sets)):
+        assert rel(gpu["phi"][k], ref["phi"][k]) < TOL, k
+    assert gpu["stats"]["rows_per_step"] == 1 and gpu["stats"]["tile_g"] == tile_g
+
+
 @pytest.mark.parametrize("tile_g", [-1, 1, 2, 4])
 @pytest.mark.parametrize("rows", [0, 1, 2, 4])
 def test_work_item_size_does_not_change_results(rom, tile_g, rows):
