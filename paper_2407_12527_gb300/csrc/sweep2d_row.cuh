@@ -84,7 +84,17 @@ __device__ __forceinline__ float2 rshfl(float2 v)
 {
     return make_float2(rshfl<DOWN>(v.x), rshfl<DOWN>(v.y));
 }
-__device__ __forceinline__ void rld8(const float *p, float (&v)[kCols]) { ldg8_early(p, v); }
+// A row for a later step: with one or two ordinates per item a coherent load, which
+// stays in order with the moment reductions issued before it and so keeps its place
+// PD steps ahead of its use (the read-only .nc form measured 4-5% slower there); with
+// four ordinates the .nc form measured faster.  The rows are not written during the
+// sweep, so both forms read the same values.
+template <int G>
+__device__ __forceinline__ void rld8(const float *p, float (&v)[kCols])
+{
+    if constexpr (G == 4) ldg8_early(p, v);
+    else ld8_volatile(p, v);
+}
 // adds 8 moments to the accumulator; a lane that owns no cells adds nothing (the
 // reductions are predicated off, not branched around)
 __device__ __forceinline__ void rred8(float *p, const float (&v)[kCols], bool on)
@@ -275,7 +285,7 @@ __device__ __forceinline__ void row_item(const SweepArgs &A, const SweepItem &it
         const int jl = k - d;
         if (on && jl >= 0 && jl < J)
 #pragma unroll
-            for (int m = 0; m < NA; ++m) rld8(arr[m] + row0 + (long long)jl * rs, buf[k][m]);
+            for (int m = 0; m < NA; ++m) rld8<G>(arr[m] + row0 + (long long)jl * rs, buf[k][m]);
     }
     __shared__ T xbuf[MULTI ? 2 : 1][MULTI ? kMaxWarps : 1][N];
     T xin[N];
@@ -309,7 +319,7 @@ __device__ __forceinline__ void row_item(const SweepArgs &A, const SweepItem &it
                 if (!CK || (on && jp >= 0 && jp < J))
 #pragma unroll
                     for (int m = 0; m < NA; ++m)
-                        rld8(arr[m] + row0 + (long long)jp * rs, buf[(u + PD) % (PD + 1)][m]);
+                        rld8<G>(arr[m] + row0 + (long long)jp * rs, buf[(u + PD) % (PD + 1)][m]);
             }
             T xo[N];
             if (!CK || (on && jl >= 0 && jl < J)) {
