@@ -872,7 +872,9 @@ int enqueue_iteration(rom_ctx *ctx, cudaStream_t st, bool use_cond, cudaGraphCon
     ca.I = ctx->I;
     ca.NXP = ctx->NXP;
     ca.MOM = ctx->MOM == 0 ? 1 : ctx->MOM;
-    ca.chunks = ctx->chunks;
+    // about four combine blocks per SM over the whole launch (the launcher evens out
+    // the passes per thread)
+    ca.chunks = (int)std::max<long long>(1, (4LL * ctx->sm_count + ctx->S - 1) / ctx->S);
     ca.cells = padded_cells(ctx);
     ca.g = (float)ctx->g;
     ca.acc = (float *)ctx->part.p;
@@ -1796,10 +1798,10 @@ int rom_solve(rom_ctx *ctx, rom_stats *stats_out)
         if ((rc = upload_inflow(ctx))) return rc;
         invalidate_graph(ctx);
     }
-    // residual chunks: combine blocks of 256 threads per sample, each thread
-    // taking one or more 8-cell sectors; about 16 blocks per SM in all, so that
-    // large grids stream many sectors per thread instead of paying the block's
-    // reduction per sector
+    // residual chunks of the 3D combine: blocks of 256 threads per sample, each
+    // thread taking one or more 8-cell sectors; about 16 blocks per SM in all, so
+    // that large grids stream many sectors per thread instead of paying the block's
+    // reduction per sector (the X-Y combine sizes its own grid)
     const long long max_chunks = std::max<long long>(1, (cells / 8 + 255) / 256);
     const long long want = std::max<long long>(1, (16LL * ctx->sm_count + ctx->S - 1) / ctx->S);
     const int chunks = (int)std::min(max_chunks, want);

@@ -92,7 +92,8 @@ struct SweepArgs {
 // reductions; the combine reads and clears them).
 
 struct CombineArgs {
-    int S, MOM, chunks;
+    int S, MOM;
+    int chunks;                 // at most this many blocks per sample
     int I, NXP;                 // columns and row pitch (min phi skips padding columns)
     long long cells;
     float g;                    // linear-kernel asymmetry (MOM = 3)
